@@ -1,0 +1,371 @@
+"""Pins of the FP64 oracle against closed forms, invariants and brute force.
+
+Each test fixes something the paper or the mathematics determines, chosen so
+that a plausible mistake in the oracle (a dropped term, a wrong sign, a
+transposed axis, a wrong normalisation) fails at least one of them.  None of
+them compares the oracle with itself.
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import hom_oracle as O
+from paper_1903_02581_gb300 import workloads as W
+
+
+def small(**kw):
+    base = dict(nx=16, ny=16, dx=0.5, dy=0.5, B=1.0, omega=1.0, dt=0.02,
+                qpc_h=1.0, qpc_w=1.5, lam=1.0, soft=0.5)
+    base.update(kw)
+    return O.Model(**base)
+
+
+def ip(a, b, m):
+    return np.sum(np.conj(a) * b) * m.dV
+
+
+# --- I1: the discrete Fourier transform -------------------------------------
+
+def test_dft_matches_library_fft():
+    a = W.random_state((8, 16, 4, 32), seed=1)
+    for ax in range(4):
+        got = O.dft_axis(a, ax)
+        ref = np.fft.fft(a, axis=ax)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+        back = O.dft_axis(got, ax, inverse=True)
+        assert np.max(np.abs(back - a)) <= 1e-13 * np.max(np.abs(a))
+
+
+def test_grid_and_wavenumber_conventions():
+    x = O.coords(16, 0.5)
+    assert np.allclose(x, -x[::-1], atol=0, rtol=0) and abs(x[0] + 3.75) < 1e-15
+    k = O.wavenumbers(16, 0.5)
+    assert np.allclose(k, 2 * np.pi * np.fft.fftfreq(16, d=0.5), rtol=0, atol=1e-14)
+    assert k[8] < 0                       # Nyquist mode taken negative (R4)
+
+
+# --- I2 / I3 / I9: unitarity, exchange antisymmetry, time reversal ----------
+
+def test_norm_conserved_on_random_state():
+    m = small()
+    psi = W.random_state((16, 16, 16, 16), seed=2)
+    n0 = np.sum(np.abs(psi) ** 2)
+    out = O.propagate(psi, m, 10)
+    assert abs(np.sum(np.abs(out) ** 2) / n0 - 1.0) <= 1e-12
+
+
+def slater_pair(m, exch=-1, sigma=1.0, xs=2.0, energy=2.5):
+    ka = O.k0_from_energy(energy, m.B, m.omega, +1)
+    kb = O.k0_from_energy(energy, m.B, m.omega, -1)
+    a = O.edge_packet(m, -xs, sigma, ka)
+    b = O.edge_packet(m, +xs, sigma, kb)
+    return a, b, O.two_particle(a, b, exch, m.dV)
+
+
+def test_exchange_antisymmetry_preserved():
+    m = small()
+    _, _, psi = slater_pair(m)
+    out = O.propagate(psi, m, 20)
+    swapped = np.transpose(out, (2, 3, 0, 1))
+    assert np.max(np.abs(out + swapped)) <= 1e-13 * np.max(np.abs(out))
+    assert np.max(np.abs(out)) > 0.01
+
+
+def test_time_reversal():
+    m = small()
+    psi = W.random_state((16, 16, 16, 16), seed=3)
+    back = O.strang_step(O.strang_step(psi, m), m, dt=-m.dt)
+    assert np.max(np.abs(back - psi)) <= 1e-12 * np.max(np.abs(psi))
+
+
+# --- I4: zero Coulomb factorises into independently propagated packets ------
+
+def test_zero_coulomb_is_slater_of_propagated_packets():
+    m = small(lam=0.0)
+    a, b, psi = slater_pair(m)
+    out = O.propagate(psi, m, 25)
+    a_t = O.propagate_2d(a, m, 25)
+    b_t = O.propagate_2d(b, m, 25)
+    ref = O.two_particle(a_t, b_t, -1, m.dV)
+    # same normalisation constant at t and at 0 (unitary, swap-symmetric)
+    scale = np.sum(np.abs(ref) ** 2) / np.sum(np.abs(out) ** 2)
+    assert abs(scale - 1.0) < 1e-12
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+# --- I5: free Gaussian spreading (B = 0, V = 0: the splitting is exact) -----
+
+def test_free_gaussian_spreading_closed_form():
+    m = O.Model(nx=32, ny=8, dx=0.4, dy=0.5, B=0.0, omega=0.0, dt=0.25,
+                qpc_h=0.0, lam=0.0)
+    s0 = 0.5
+    x = O.coords(m.nx, m.dx)
+    y = O.coords(m.ny, m.dy)
+    gx = np.exp(-x ** 2 / (4 * s0 ** 2))
+    gy = np.exp(-y ** 2 / 2.0)
+    phi = np.outer(gx, gy).astype(np.complex128)
+    phi /= math.sqrt(np.sum(np.abs(phi) ** 2) * m.dx * m.dy)
+    psi = np.einsum("ab,cd->abcd", phi, phi)
+    t = 0.5
+    out = O.propagate(psi, m, 2)                     # two steps of 0.25
+    rho_x1 = np.sum(np.abs(out) ** 2, axis=(1, 2, 3)) * m.dV / m.dx
+    mean = np.sum(x * rho_x1) * m.dx
+    var = np.sum((x - mean) ** 2 * rho_x1) * m.dx
+    exact = s0 ** 2 * (1.0 + t ** 2 / (4.0 * s0 ** 4))
+    assert abs(mean) < 1e-12
+    assert abs(var - exact) <= 1e-10
+
+
+# --- I7: Landau levels, cyclotron motion, hybrid edge levels ----------------
+
+def eigen_product(m, k1, k2):
+    """Product of two single-k lowest hybrid states e^{ikx} phi_k(y)."""
+    x = O.coords(m.nx, m.dx)
+    y = O.coords(m.ny, m.dy)
+    om = O.hybrid_omega(m.B, m.omega)
+
+    def one(k):
+        phi = np.exp(1j * k * x)[:, None] * np.exp(-0.5 * om * (y - k * m.B / om ** 2) ** 2)[None, :]
+        return phi / math.sqrt(np.sum(np.abs(phi) ** 2) * m.dx * m.dy)
+
+    return np.einsum("ab,cd->abcd", one(k1), one(k2))
+
+
+def level_energy(m, k):
+    om = O.hybrid_omega(m.B, m.omega)
+    return 0.5 * om + k * k * m.omega ** 2 / (2 * om ** 2)
+
+
+@pytest.mark.parametrize("B,omega", [(1.0, 0.0), (1.0, 1.0), (1.5, 0.5)])
+def test_level_phase_converges_at_second_order(B, omega):
+    m = O.Model(nx=8, ny=32, dx=0.5, dy=0.4, B=B, omega=omega, qpc_h=0.0, lam=0.0)
+    k = O.wavenumbers(m.nx, m.dx)
+    k1, k2 = k[1], k[7]                               # +pi/4 and -pi/4
+    psi0 = eigen_product(m, k1, k2)
+    E = level_energy(m, k1) + level_energy(m, k2)
+    # exact energy of the discrete state (spectral accuracy)
+    obs = O.observables(psi0, m)
+    assert abs(obs["energy"] - E) <= 1e-10
+    T = 1.0
+    errs = []
+    for n in (20, 40):
+        out = O.propagate(psi0, m, n, dt=T / n)
+        errs.append(abs(ip(psi0, out, m) - np.exp(-1j * E * T)))
+    ratio = errs[0] / errs[1]
+    assert 3.6 < ratio < 4.4, (errs, ratio)
+    assert errs[1] < 1e-3
+
+
+def test_cyclotron_half_period():
+    m = O.Model(nx=8, ny=32, dx=0.5, dy=0.4, B=1.0, omega=0.0, qpc_h=0.0, lam=0.0)
+    y = O.coords(m.ny, m.dy)
+    A = 1.0
+    shifted = np.ones((m.nx, 1)) * np.exp(-0.5 * (y - A) ** 2)[None, :]
+    ground = np.ones((m.nx, 1)) * np.exp(-0.5 * y ** 2)[None, :]
+    psi0 = np.einsum("ab,cd->abcd", shifted, ground).astype(np.complex128)
+    psi0 /= math.sqrt(np.sum(np.abs(psi0) ** 2) * m.dV)
+    # <y1>(t) = A cos(B t).  At the quarter period the splitting's O(dt^2)
+    # frequency shift shows at first order; at the half period only at second.
+    def y1_at(t, n):
+        out = O.propagate(psi0, m, n, dt=t / n)
+        rho_y1 = np.sum(np.abs(out) ** 2, axis=(0, 2, 3)) * m.dV
+        return np.sum(y * rho_y1)
+
+    errs = [abs(y1_at(math.pi / 2, n)) for n in (12, 24)]
+    assert errs[1] < 2e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+    half = [abs(y1_at(math.pi, n) + A) for n in (24, 48)]
+    assert half[1] < 1e-5 and half[0] / half[1] > 12.0, half
+
+
+# --- I8: Strang is second order, the printed (Lie) product first order ------
+
+def test_splitting_orders():
+    m = small(dt=0.04)
+    _, _, psi = slater_pair(m)
+    T = 0.32
+    ref = O.propagate(psi, m, 64, dt=T / 64)
+    e = {}
+    for order in ("strang", "lie"):
+        e[order] = [np.max(np.abs(O.propagate(psi, m, n, order=order, dt=T / n) - ref))
+                    for n in (4, 8)]
+    rs = e["strang"][0] / e["strang"][1]
+    rl = e["lie"][0] / e["lie"][1]
+    assert 3.5 < rs < 4.5, e
+    assert 1.7 < rl < 2.3, e
+
+
+# --- energy conservation ties the propagator's V and T to the observable ----
+
+def test_energy_conserved_to_second_order():
+    m = small()
+    _, _, psi = slater_pair(m)
+    e0 = O.observables(psi, m)["energy"]
+    T = 0.4
+    drifts = []
+    for n in (10, 20):
+        out = O.propagate(psi, m, n, dt=T / n)
+        drifts.append(abs(O.observables(out, m)["energy"] - e0))
+    assert drifts[1] < 1e-3
+    assert 3.0 < drifts[0] / drifts[1] < 5.0, drifts
+
+
+def test_energy_terms_change_sign_with_coulomb_strength():
+    m = small()
+    _, _, psi = slater_pair(m)
+    o1 = O.observables(psi, m)
+    o2 = O.observables(psi, small(lam=-1.0))
+    assert o1["e_coul"] > 0 and abs(o1["e_coul"] + o2["e_coul"]) < 1e-14
+    assert abs(o1["e_pot"] - o2["e_pot"]) < 1e-14
+
+
+# --- Coulomb expectation by independent quadrature (Eq. coulomb) ------------
+
+def test_coulomb_expectation_matches_quadrature():
+    m = O.Model(nx=32, ny=32, dx=0.25, dy=0.25, lam=1.0, soft=1.2)
+    s = 0.35
+    ca, cb = (-0.6, 0.0), (0.6, 0.3)
+    x = O.coords(m.nx, m.dx)
+    y = O.coords(m.ny, m.dy)
+
+    def g(c):
+        phi = np.exp(-((x[:, None] - c[0]) ** 2 + (y[None, :] - c[1]) ** 2) / (4 * s * s))
+        return (phi / math.sqrt(np.sum(phi ** 2) * m.dx * m.dy)).astype(np.complex128)
+
+    psi = np.einsum("ab,cd->abcd", g(ca), g(cb))
+    got = O.observables(psi, m)["e_coul"]
+    # relative coordinate R = r1 - r2 ~ N(ca - cb, 2 s^2 I)
+    mu = (ca[0] - cb[0], ca[1] - cb[1])
+    v = 2 * s * s
+
+    def f(ry, rx):
+        pdf = math.exp(-((rx - mu[0]) ** 2 + (ry - mu[1]) ** 2) / (2 * v)) / (2 * math.pi * v)
+        return pdf / math.sqrt(rx * rx + ry * ry + m.soft ** 2)
+
+    L = 8 * math.sqrt(v)
+    ref, _ = integrate.dblquad(f, mu[0] - L, mu[0] + L, mu[1] - L, mu[1] + L,
+                               epsabs=1e-13, epsrel=1e-12)
+    assert abs(got - ref) <= 1e-9 * ref
+
+
+# --- packet construction (Eq. singlepwp, R6) --------------------------------
+
+def test_packet_energy_closed_form():
+    m = O.Model(nx=64, ny=32, dx=0.5, dy=0.4, B=1.0, omega=1.0, qpc_h=0.0, lam=0.0)
+    sigma = 1.5
+    k0 = O.k0_from_energy(2.5, m.B, m.omega, +1)
+    assert abs(level_energy(m, k0) - 2.5) < 1e-14
+    phi = O.edge_packet(m, -3.0, sigma, k0)
+    om = O.hybrid_omega(m.B, m.omega)
+    exact = 0.5 * om + m.omega ** 2 / (2 * om ** 2) * (k0 ** 2 + 1.0 / (4 * sigma ** 2))
+    assert abs(O.energy_2d(phi, m) - exact) <= 1e-9
+    # centre of the x-marginal
+    x = O.coords(m.nx, m.dx)
+    rho = np.sum(np.abs(phi) ** 2, axis=1) * m.dy
+    assert abs(np.sum(x * rho) * m.dx + 3.0) < 1e-9
+
+
+def test_packet_direction_and_edge():
+    m = O.Model(nx=64, ny=32, dx=0.5, dy=0.4)
+    y = O.coords(m.ny, m.dy)
+    for d in (+1, -1):
+        k0 = O.k0_from_energy(2.5, m.B, m.omega, d)
+        phi = O.edge_packet(m, 0.0, 1.5, k0)
+        rho_y = np.sum(np.abs(phi) ** 2, axis=0) * m.dx
+        yc = np.sum(y * rho_y) * m.dy
+        assert np.sign(yc) == d and abs(yc - k0 / 2.0) < 0.05
+
+
+def test_two_particle_slater_vanishes_on_diagonal():
+    m = small()
+    _, _, psi = slater_pair(m)
+    n = m.nx * m.ny
+    flat = psi.reshape(n, n)
+    assert np.max(np.abs(np.diag(flat))) <= 1e-15 * np.max(np.abs(flat))
+    assert abs(np.sum(np.abs(psi) ** 2) * m.dV - 1.0) < 1e-13
+
+
+# --- I6: exchange-sum identity with Coulomb on ------------------------------
+
+def test_exchange_sum_identity():
+    m = small()
+    a, b, _ = slater_pair(m)
+    prod = O.two_particle(a, b, 0, m.dV)
+    ov = abs(np.sum(np.conj(a) * b) * m.dx * m.dy) ** 2
+    n = 15
+    pp = O.bunching(O.propagate(prod, m, n), m)
+    total = 0.0
+    for s in (+1, -1):
+        st = O.two_particle(a, b, s, m.dV)
+        total += (1 + s * ov) * O.bunching(O.propagate(st, m, n), m)
+    assert abs(total - 2 * pp) <= 1e-12
+
+
+def test_bunching_counts_same_side_pairs():
+    m = small()
+    x = O.coords(m.nx, m.dx)
+    y = O.coords(m.ny, m.dy)
+
+    def blob(xc):
+        phi = np.exp(-((x[:, None] - xc) ** 2 + y[None, :] ** 2) / 0.1).astype(np.complex128)
+        return phi / math.sqrt(np.sum(np.abs(phi) ** 2) * m.dx * m.dy)
+
+    left, right = blob(-2.0), blob(2.0)
+    assert O.bunching(O.two_particle(left, left, 0, m.dV), m) > 1 - 1e-12
+    assert O.bunching(O.two_particle(right, right, 0, m.dV), m) > 1 - 1e-12
+    assert O.bunching(O.two_particle(left, right, 0, m.dV), m) < 1e-12
+    # half of a particle on each side, the other one left: P_b = 1/2
+    both = (left + right) / math.sqrt(2.0)
+    assert abs(O.bunching(O.two_particle(both, left, 0, m.dV), m) - 0.5) < 1e-12
+
+
+def test_bunching_is_half_for_uniform_density():
+    m = small()
+    psi = np.ones((16, 16, 16, 16), dtype=np.complex128)
+    psi /= math.sqrt(np.sum(np.abs(psi) ** 2) * m.dV)
+    assert abs(O.bunching(psi, m) - 0.5) < 1e-14
+
+
+# --- I10: adjoint ------------------------------------------------------------
+
+def test_adjoint_dot_product():
+    m = small()
+    u = W.random_state((16, 16, 16, 16), seed=4)
+    v = W.random_state((16, 16, 16, 16), seed=5)
+    lhs = np.sum(np.conj(O.strang_step(u, m)) * v)
+    rhs = np.sum(np.conj(u) * O.strang_step(v, m, dt=-m.dt))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    m = small(dt=0.05)
+    n = 12
+    xs, sig, delay = 2.0, 1.0, 0.0
+    ka = O.k0_from_energy(2.5, m.B, m.omega, +1)
+    kb = O.k0_from_energy(2.5, m.B, m.omega, -1)
+
+    def state(dl):
+        a = O.edge_packet(m, -xs, sig, ka)
+        b = O.edge_packet(m, xs + dl, sig, kb)
+        return a, b, O.two_particle(a, b, -1, m.dV)
+
+    a, b, psi0 = state(delay)
+    db = O.edge_packet_dx0(m, xs + delay, sig, kb)
+    dpsi = O.slater_dstate(a, b, db, -1, m.dV)
+    loss, grad = O.loss_and_gradient(psi0, dpsi, m, n)
+
+    def L(mm, p0):
+        return O.bunching(O.propagate(p0, mm, n), mm)
+
+    h = 1e-4
+    fd = {
+        "h": (L(small(dt=0.05, qpc_h=1.0 + h), psi0) - L(small(dt=0.05, qpc_h=1.0 - h), psi0)) / (2 * h),
+        "w": (L(small(dt=0.05, qpc_w=1.5 + h), psi0) - L(small(dt=0.05, qpc_w=1.5 - h), psi0)) / (2 * h),
+        "delay": (L(m, state(delay + h)[2]) - L(m, state(delay - h)[2])) / (2 * h),
+    }
+    assert abs(loss - L(m, psi0)) < 1e-14
+    for k, v in fd.items():
+        assert abs(grad[k] - v) <= 1e-6 * max(abs(v), 1e-3), (k, grad[k], v)
