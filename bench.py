@@ -1,0 +1,334 @@
+"""Benchmark: 4D grid-point updates/s of the two-electron Strang propagation.
+
+Workload (default): the full-scale configuration, 256x64 grid per electron
+(268,435,456 points, complex64 state of 2 GiB, larger than the 129 MB L2),
+dt = 0.002, Coulomb strength 1 (softening 0.25), QPC height 1 / width 2,
+packets of energy 3 started at x = -24 / +24.  One bench "step" is one pass
+of the hot path at the workload's observation cadence: 100 Strang steps
+(two kinetic passes each, potential phase fused) followed by one evaluation
+of the observables (norm, energy terms, bunching probability).
+
+  value  = whole-job grid-point updates per second (points x Strang steps /
+           time), inputs resident in HBM, max time over ranks;
+  e2e    = the same metric through the C ABI with the state copied from
+           pinned host memory every step and the observables read back;
+  roofline = the dominant kernel's algorithmic bytes (16 B per point per pass
+           in complex64: one read, one write) over its average CUDA-event
+           duration, against the measured HBM copy bandwidth;
+  cpu_baseline = the FP64 oracle on the machine's host cores on a bounded sample.
+
+Multi-GPU: one process per GPU (torchrun); each rank propagates its own
+simulation (weak scaling), no collective on the data path.
+``--impl reference`` times the oracle (the only reference this method has).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+INNER = 100          # Strang steps per bench step (the observation cadence)
+SAMPLE_NY = 32       # oracle sample: the full-scale workload at 256 x 32 per electron
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--inner", type=int, default=INNER)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1903_02581_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".inc", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when the summary was taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    v = vals.get(f"{kernel}_dram_bytes_per_launch_full_scale")
+    return float(v) if v else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for i, nm in enumerate(names):
+                    if r[5 + i].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_rate(steps: int = 1):
+    """FP64 oracle on the bounded sample; returns (updates/s, seconds, description)."""
+    import numpy as np
+
+    from oracle import adapter as A
+    from oracle import hom_oracle as O
+    from paper_1903_02581_gb300 import workloads as W
+
+    w = W.fullscale(sigma=2.0)
+    w = W.shrink(w, ny=SAMPLE_NY)
+    w["dy"] = 0.25
+    sim = w["sims"][0]
+    m = A.model_for(w, sim)
+    psi = A.initial_state(w, sim)
+    V = O.v_total(m)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        psi = O.strang_step(psi, m, vtot=V)
+    sec = time.perf_counter() - t0
+    pts = (w["nx"] * w["ny"]) ** 2
+    desc = (f"oracle Strang step(s) on the full-scale workload at 256x{SAMPLE_NY} per electron "
+            f"({pts:,} points, FP64, numpy), {steps} step(s); per-point work of the x transforms as at "
+            f"256x64, y transforms half as long")
+    assert np.isfinite(psi).all()
+    return pts * steps / sec, sec, desc
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample_rate(1)
+    rates, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        r, s, desc = oracle_sample_rate(1)
+        rates.append(r)
+        secs += s
+    value = len(rates) / sum(1.0 / r for r in rates)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "4D grid-point updates/s (Strang split-step, two electrons)",
+        "value": value, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / len(rates), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fullscale-256x64-sampled", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def gb300_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1903_02581_gb300 import binding as H
+    from paper_1903_02581_gb300 import build as Bd
+    from paper_1903_02581_gb300 import workloads as W
+
+    if rank == 0:
+        Bd.build()
+    if world > 1:
+        dist.barrier()
+    H.lib()
+
+    sigma = [2.0, 1.0, 4.0][rank % 3]
+    w = W.fullscale(sigma=sigma)
+    pts = (w["nx"] * w["ny"]) ** 2
+    batch = len(w["sims"])
+    pr = H.Propagator(w, device=f"cuda:{local}")
+    stream = pr.stream
+
+    def bench_step():
+        pr.step(args.inner)
+        return pr.observables()
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    H.hom_profile(pr.ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    obs = None
+    for _ in range(args.steps):
+        obs = bench_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    prof = H.hom_profile_read(pr.ctx)
+    H.hom_profile(pr.ctx, False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * batch * pts * args.inner * args.steps / (ms_max / 1000.0)
+
+    # dominant kernel and its roofline (algorithmic bytes: 1 read + 1 write of the state per pass)
+    algo_bytes = batch * pts * 8 * 2
+    k_row = prof["ms_row"] / max(prof["n_row"], 1)
+    k_col = prof["ms_col"] / max(prof["n_col"], 1)
+    name, avg_ms = ("kinetic_pass_col", k_col) if prof["ms_col"] >= prof["ms_row"] else ("kinetic_pass_row", k_row)
+    peak, peak_kind = load_peaks()
+    achieved = algo_bytes / (avg_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(name), "kernel": name, "peak_source": peak_kind,
+                "row_pass_ms": k_row, "col_pass_ms": k_col,
+                "row_pass_frac": algo_bytes / (k_row / 1000.0) / 1e9 / peak,
+                "col_pass_frac": algo_bytes / (k_col / 1000.0) / 1e9 / peak}
+
+    # end to end through the C ABI: host state in pinned memory copied in every step
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((pts,), dtype=torch.complex64, pin_memory=True)
+        hview = host.numpy()
+        H.hom_copy_state(pr.ctx, 0, hview, to_device=False)
+        nrep = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(nrep):
+            H.hom_copy_state(pr.ctx, 0, hview, to_device=True)
+            pr.step(args.inner)
+            pr.observables()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        sec_t = torch.tensor([sec], dtype=torch.float64, device=f"cuda:{local}")
+        if world > 1:
+            dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * batch * pts * args.inner * nrep / float(sec_t.item()), "unit": "updates/s",
+               "h2d_bytes_per_step": int(hview.nbytes), "d2h_bytes_per_step": 48 * batch, "steps": nrep}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sec, desc = oracle_sample_rate(1)
+        cpu = {"value": rate, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "seconds": sec}
+
+    launches = args.steps * (2 * args.inner + 4)
+    if rank == 0:
+        line = {
+            "metric": "4D grid-point updates/s (Strang split-step, two electrons)",
+            "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fullscale-256x64", "nx": w["nx"], "ny": w["ny"], "points_per_sim": pts,
+                       "sims_per_gpu": batch, "state": "complex64", "strang_steps_per_step": args.inner,
+                       "observables_per_step": 1, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (2 GiB state), no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "p_bunch_last": obs[0]["p_bunch"] if obs else None,
+            "norm_last": obs[0]["norm"] if obs else None,
+        }
+        print(json.dumps(line), flush=True)
+    pr.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gb300_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * hom.h -- C ABI of libhom: Strang split-step Fourier propagation of the
+ * two-electron wavefunction psi(x1,y1,x2,y2) of a Hong-Ou-Mandel
+ * interferometer built from quantum-Hall edge states, on one GPU.
+ *
+ * The operation follows Bellentani, Bordone, Oriols, Bertoni,
+ * arXiv:1903.02581: Sec. II.C (two-particle Hamiltonian in the Landau gauge,
+ * Eq. evoloperat, parallel 2D Fourier transforms), Appendix A (regrouping of
+ * the magnetic kinetic term, Eq. 2PTB), Eq. coulomb (softened interaction),
+ * Eq. twopstate (Slater determinant), Eq. singlepwp (edge-state packets) and
+ * Eq. p_bunching (bunching probability).
+ *
+ * Conventions (units hbar = m* = |e| = 1).  Axes are relabelled with respect
+ * to the paper: propagation runs along x, the edge confinement along y.
+ *   H_i  = 1/2 (p_x - B y_i)^2 + 1/2 p_y^2 + V1(x_i, y_i)
+ *   V1   = 1/2 omega_y^2 y^2 + qpc_h exp(-(x - qpc_x0)^2 / (2 qpc_w^2))
+ *   V12  = coul_lambda / sqrt((x1-x2)^2 + (y1-y2)^2 + coul_soft^2)
+ *   grid x_j = (j - (nx-1)/2) dx (cell-centred, same for y), k_m = 2 pi m /
+ *   (n d) with m in [-n/2, n/2); periodic box; plain coordinate differences.
+ *   One step S(dt) = e^{-iV dt/2} F_x^-1 e^{-iT_x dt/2} F_y^-1 e^{-iT_y dt}
+ *   F_y e^{-iT_x dt/2} F_x e^{-iV dt/2}, with T_x diagonal in (k_x, y) and
+ *   T_y in k_y (Eq. evoloperat in symmetric order).
+ *
+ * State layout (device, owned by the caller): psi[b][x1][y1][x2][y2],
+ * y2 fastest, interleaved complex (re, im) of float (HOM_C64) or double
+ * (HOM_C128); batch b indexes independent simulations.  The state is
+ * normalised so that sum |psi|^2 dx^2 dy^2 = 1.
+ *
+ * Errors: every call returns a hom_status; nothing aborts.  hom_last_error()
+ * gives a message for the last failure on a context.  After HOM_ERR_CUDA or
+ * HOM_ERR_TIMEOUT the context is poisoned: further calls return
+ * HOM_ERR_STATE until hom_destroy.  A context is not thread-safe.
+ */
+#ifndef HOM_H
+#define HOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HOM_OK = 0,
+  HOM_ERR_ARG = 1,      /* invalid argument (size, value, pointer)          */
+  HOM_ERR_STATE = 2,    /* poisoned context or call out of order            */
+  HOM_ERR_CUDA = 3,     /* a CUDA call failed (message in hom_last_error)   */
+  HOM_ERR_NOMEM = 4,    /* workspace smaller than hom_workspace_bytes()     */
+  HOM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                    */
+  HOM_ERR_NUMERIC = 6   /* non-finite value detected in a reduction         */
+} hom_status;
+
+typedef enum { HOM_C64 = 0, HOM_C128 = 1 } hom_prec;
+
+/* Plain data, copied by hom_create.  nx in {16,32,64,128,256}, ny in
+ * {16,32,64}; HOM_C128 needs nx*ny <= 8192.  dt may be negative (backward
+ * propagation).  qpc_h, qpc_w and coul_lambda are defaults for every
+ * simulation of the batch (see hom_set_sim_params).  ckpt_slots reserves
+ * room in the workspace for that many state checkpoints of hom_backward
+ * (0 if hom_backward is not used). */
+typedef struct {
+  int32_t nx, ny, batch, prec;
+  double dx, dy, B, omega_y, dt;
+  double qpc_h, qpc_w, qpc_x0;
+  double coul_lambda, coul_soft;
+  int32_t observe_every;   /* informational: caller's observation cadence */
+  int32_t ckpt_slots;
+} hom_params;
+
+/* One edge packet (Eq. singlepwp): centre x0, width sigma (standard
+ * deviation of |psi|^2 along x), and either the energy of the central
+ * wavevector on the lowest hybrid level (by_k0 == 0; needs omega_y > 0 and
+ * energy >= sqrt(B^2+omega_y^2)/2; dir = +1 moves towards +x, -1 towards -x)
+ * or the central wavevector k0 itself (by_k0 != 0, dir ignored). */
+typedef struct {
+  double x0, sigma, energy, k0;
+  int32_t dir, by_k0;
+} hom_packet;
+
+/* Observables of one simulation (host, FP64): norm = sum |psi|^2 dV;
+ * e_kin = <T_x + T_y> (both particles); e_pot = <V1(r1) + V1(r2)>;
+ * e_coul = <V12>; energy = e_kin + e_pot + e_coul; p_bunch = probability
+ * that x1 and x2 have the same sign (Eq. p_bunching with the two regions
+ * x < 0 and x > 0).  Expectations are not divided by the norm. */
+typedef struct {
+  double norm, energy, e_kin, e_pot, e_coul, p_bunch;
+} hom_obs;
+
+typedef struct hom_ctx hom_ctx;
+
+/* Bytes of one batch of states: batch * (nx*ny)^2 * sizeof(complex).  Returns
+ * 0 for invalid parameters. */
+size_t hom_state_bytes(const hom_params* p);
+
+/* Bytes of device workspace hom_create needs (tables, reduction partials,
+ * packet buffers, ckpt_slots checkpoints).  Returns 0 for invalid parameters. */
+size_t hom_workspace_bytes(const hom_params* p);
+
+/* Create a context.  d_state (hom_state_bytes) and d_workspace
+ * (workspace_bytes >= hom_workspace_bytes) are device pointers owned by the
+ * caller, 256-byte aligned, and must outlive the context; the context
+ * allocates no device memory.  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream) on which every launch and copy of the context is ordered.
+ * Builds the FP64 phase tables (arguments reduced mod 2 pi) and uploads them;
+ * synchronises the stream before returning.  The state is not touched. */
+hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace,
+                      size_t workspace_bytes, void* cuda_stream, hom_ctx** out);
+
+/* Override the QPC height/width and Coulomb strength of simulation b and
+ * rebuild its tables (synchronises the stream). */
+hom_status hom_set_sim_params(hom_ctx* ctx, int32_t b, double qpc_h, double qpc_w,
+                              double coul_lambda);
+
+/* Set simulation b (b = -1: every simulation) to
+ *   psi = c [alpha(r1) beta(r2) + exch * beta(r1) alpha(r2)]
+ * with exch = -1 (Slater determinant, Eq. twopstate), +1 (symmetric) or 0
+ * (product), c fixing sum |psi|^2 dV = 1.  The packets are built on the host
+ * in FP64 and combined on the device.  Synchronises the stream. */
+hom_status hom_init_packets(hom_ctx* ctx, int32_t b, const hom_packet* alpha,
+                            const hom_packet* beta, int32_t exch);
+
+/* Advance every simulation by nsteps Strang steps (nsteps >= 0), state in
+ * real space before and after.  Asynchronous on the context's stream. */
+hom_status hom_step(hom_ctx* ctx, int32_t nsteps);
+
+/* Compute the observables of every simulation; out has batch entries (host).
+ * FP64 reductions; synchronises the stream.  HOM_ERR_NUMERIC if the norm is
+ * not finite. */
+hom_status hom_observables(hom_ctx* ctx, hom_obs* out);
+
+/* Adjoint gradient of L_b = p_bunch of simulation b after nsteps steps.
+ * Starts from the current state, which must have been set by
+ * hom_init_packets (the packets define d psi0 / d delay, delay being the
+ * centre of beta); keeps checkpoints every K steps in the workspace
+ * (ceil(nsteps/K) <= ckpt_slots), recomputes each segment forward and runs
+ * the adjoint step S(dt)^dagger = S(-dt) backward.  loss[b] = L_b,
+ * grad[3*b + {0,1,2}] = dL_b / d{qpc_h, qpc_w, delay} (host arrays).  Leaves
+ * the state at step nsteps.  Synchronises the stream. */
+hom_status hom_backward(hom_ctx* ctx, int32_t nsteps, int32_t K, double* loss,
+                        double* grad);
+
+/* Copy simulation b between the device state and host memory (to_device != 0:
+ * host -> device).  bytes must equal (nx*ny)^2 * sizeof(complex).  Layout as
+ * the device state.  Synchronises the stream. */
+hom_status hom_copy_state(hom_ctx* ctx, int32_t b, void* host, size_t bytes,
+                          int32_t to_device);
+
+/* Instrumentation.  While enabled, hom_step records a pair of CUDA events on
+ * the context's stream around every kinetic-pass launch (row pass: particle 2,
+ * column pass: particle 1); hom_profile_read synchronises the stream and
+ * returns the summed device milliseconds and launch counts of each pass since
+ * the last enable.  Enabling resets the sums.  Costs two event records per
+ * launch; no effect on results. */
+hom_status hom_profile(hom_ctx* ctx, int32_t enable);
+hom_status hom_profile_read(hom_ctx* ctx, double* ms_row, double* ms_col, int64_t* n_row,
+                            int64_t* n_col);
+
+/* Message of the last failure on ctx (or of the last failed hom_create when
+ * ctx is NULL); never NULL. */
+const char* hom_last_error(const hom_ctx* ctx);
+
+/* Destroy the context (does not free the caller's buffers).  NULL is a no-op. */
+void hom_destroy(hom_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOM_H */

@@ -1,0 +1,34 @@
+"""Turn a plain workload dictionary into oracle inputs (test infrastructure only).
+
+A workload is plain data (grid, time step, and per-simulation QPC, Coulomb
+and packet parameters); this module reads it and calls ``hom_oracle`` only.
+"""
+
+from __future__ import annotations
+
+from . import hom_oracle as O
+
+
+def model_for(w: dict, sim: dict | None = None) -> O.Model:
+    sim = sim or {}
+    return O.Model(nx=w["nx"], ny=w["ny"], dx=w["dx"], dy=w["dy"], B=w["B"], omega=w["omega"],
+                   dt=w["dt"], qpc_h=sim.get("qpc_h", w["qpc_h"]), qpc_w=sim.get("qpc_w", w["qpc_w"]),
+                   qpc_x0=w.get("qpc_x0", 0.0), lam=sim.get("lam", w["lam"]), soft=w["soft"])
+
+
+def packet_k0(m: O.Model, pk: dict) -> float:
+    if pk.get("by_k0", False):
+        return pk["k0"]
+    return O.k0_from_energy(pk["energy"], m.B, m.omega, pk["dir"])
+
+
+def packets(w: dict, sim: dict):
+    m = model_for(w, sim)
+    a = O.edge_packet(m, sim["alpha"]["x0"], sim["alpha"]["sigma"], packet_k0(m, sim["alpha"]))
+    b = O.edge_packet(m, sim["beta"]["x0"], sim["beta"]["sigma"], packet_k0(m, sim["beta"]))
+    return m, a, b
+
+
+def initial_state(w: dict, sim: dict):
+    m, a, b = packets(w, sim)
+    return O.two_particle(a, b, sim["exch"], m.dV)

@@ -1,0 +1,266 @@
+"""ctypes binding of libhom (include/hom.h): argument marshalling only.
+
+Every step of the propagation runs in the CUDA library; this module converts
+Python values to the C structures, passes raw device pointers owned by
+PyTorch, and turns a non-OK status into an exception.  There is no fallback:
+if the library is missing, ``lib()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+HOM_OK, HOM_ERR_ARG, HOM_ERR_STATE, HOM_ERR_CUDA, HOM_ERR_NOMEM, HOM_ERR_TIMEOUT, HOM_ERR_NUMERIC = range(7)
+HOM_C64, HOM_C128 = 0, 1
+STATUS_NAMES = ["HOM_OK", "HOM_ERR_ARG", "HOM_ERR_STATE", "HOM_ERR_CUDA", "HOM_ERR_NOMEM",
+                "HOM_ERR_TIMEOUT", "HOM_ERR_NUMERIC"]
+
+
+class hom_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("prec", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("B", ctypes.c_double),
+                ("omega_y", ctypes.c_double), ("dt", ctypes.c_double),
+                ("qpc_h", ctypes.c_double), ("qpc_w", ctypes.c_double), ("qpc_x0", ctypes.c_double),
+                ("coul_lambda", ctypes.c_double), ("coul_soft", ctypes.c_double),
+                ("observe_every", ctypes.c_int32), ("ckpt_slots", ctypes.c_int32)]
+
+
+class hom_packet(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("sigma", ctypes.c_double), ("energy", ctypes.c_double),
+                ("k0", ctypes.c_double), ("dir", ctypes.c_int32), ("by_k0", ctypes.c_int32)]
+
+
+class hom_obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("energy", ctypes.c_double), ("e_kin", ctypes.c_double),
+                ("e_pot", ctypes.c_double), ("e_coul", ctypes.c_double), ("p_bunch", ctypes.c_double)]
+
+
+OBS_KEYS = [f for f, _ in hom_obs._fields_]
+
+
+class HomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/hom.h declares."""
+    with open(os.path.join(_build.INCLUDE, "hom.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hom_[a-z_]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhom.so (built in-tree by ``build.build()``); raise if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libhom is not built ({_build.LIB} missing): run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    L.hom_state_bytes.argtypes = [P(hom_params)]
+    L.hom_state_bytes.restype = ctypes.c_size_t
+    L.hom_workspace_bytes.argtypes = [P(hom_params)]
+    L.hom_workspace_bytes.restype = ctypes.c_size_t
+    L.hom_create.argtypes = [P(hom_params), vp, vp, ctypes.c_size_t, vp, P(vp)]
+    L.hom_create.restype = ctypes.c_int
+    L.hom_set_sim_params.argtypes = [vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.hom_set_sim_params.restype = ctypes.c_int
+    L.hom_init_packets.argtypes = [vp, ctypes.c_int32, P(hom_packet), P(hom_packet), ctypes.c_int32]
+    L.hom_init_packets.restype = ctypes.c_int
+    L.hom_step.argtypes = [vp, ctypes.c_int32]
+    L.hom_step.restype = ctypes.c_int
+    L.hom_observables.argtypes = [vp, P(hom_obs)]
+    L.hom_observables.restype = ctypes.c_int
+    L.hom_backward.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double)]
+    L.hom_backward.restype = ctypes.c_int
+    L.hom_copy_state.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_size_t, ctypes.c_int32]
+    L.hom_copy_state.restype = ctypes.c_int
+    L.hom_profile.argtypes = [vp, ctypes.c_int32]
+    L.hom_profile.restype = ctypes.c_int
+    L.hom_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64),
+                                   P(ctypes.c_int64)]
+    L.hom_profile_read.restype = ctypes.c_int
+    L.hom_last_error.argtypes = [vp]
+    L.hom_last_error.restype = ctypes.c_char_p
+    L.hom_destroy.argtypes = [vp]
+    L.hom_destroy.restype = None
+    _LIB = L
+    return L
+
+
+def _check(status, ctx):
+    if status != HOM_OK:
+        msg = lib().hom_last_error(ctx)
+        raise HomError(status, msg.decode() if msg else "")
+
+
+# --- thin wrappers with the C names ----------------------------------------
+
+def hom_state_bytes(p: hom_params) -> int:
+    return lib().hom_state_bytes(ctypes.byref(p))
+
+
+def hom_workspace_bytes(p: hom_params) -> int:
+    return lib().hom_workspace_bytes(ctypes.byref(p))
+
+
+def hom_create(p: hom_params, d_state: int, d_workspace: int, workspace_bytes: int, stream: int):
+    ctx = ctypes.c_void_p()
+    _check(lib().hom_create(ctypes.byref(p), d_state, d_workspace, workspace_bytes, stream, ctypes.byref(ctx)), None)
+    return ctx
+
+
+def hom_set_sim_params(ctx, b, qpc_h, qpc_w, coul_lambda):
+    _check(lib().hom_set_sim_params(ctx, b, qpc_h, qpc_w, coul_lambda), ctx)
+
+
+def hom_init_packets(ctx, b, alpha: hom_packet, beta: hom_packet, exch: int):
+    _check(lib().hom_init_packets(ctx, b, ctypes.byref(alpha), ctypes.byref(beta), exch), ctx)
+
+
+def hom_step(ctx, nsteps: int):
+    _check(lib().hom_step(ctx, nsteps), ctx)
+
+
+def hom_observables(ctx, batch: int) -> list[dict]:
+    out = (hom_obs * batch)()
+    _check(lib().hom_observables(ctx, out), ctx)
+    return [{k: getattr(o, k) for k in OBS_KEYS} for o in out]
+
+
+def hom_backward(ctx, batch: int, nsteps: int, K: int):
+    loss = (ctypes.c_double * batch)()
+    grad = (ctypes.c_double * (3 * batch))()
+    _check(lib().hom_backward(ctx, nsteps, K, loss, grad), ctx)
+    return np.array(loss[:]), np.array(grad[:]).reshape(batch, 3)
+
+
+def hom_copy_state(ctx, b: int, host: np.ndarray, to_device: bool):
+    if not host.flags.c_contiguous:
+        raise ValueError("host array must be C-contiguous")
+    _check(lib().hom_copy_state(ctx, b, host.ctypes.data, host.nbytes, 1 if to_device else 0), ctx)
+
+
+def hom_profile(ctx, enable: bool):
+    _check(lib().hom_profile(ctx, 1 if enable else 0), ctx)
+
+
+def hom_profile_read(ctx) -> dict:
+    mr, mc = ctypes.c_double(), ctypes.c_double()
+    nr, nc = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().hom_profile_read(ctx, ctypes.byref(mr), ctypes.byref(mc), ctypes.byref(nr), ctypes.byref(nc)), ctx)
+    return dict(ms_row=mr.value, ms_col=mc.value, n_row=nr.value, n_col=nc.value)
+
+
+def hom_last_error(ctx) -> str:
+    return lib().hom_last_error(ctx).decode()
+
+
+def hom_destroy(ctx):
+    if ctx:
+        lib().hom_destroy(ctx)
+
+
+# --- convenience: parameters from a workload description -------------------
+
+def make_params(w: dict, batch: int | None = None, ckpt_slots: int = 0, dt: float | None = None) -> hom_params:
+    p = hom_params()
+    p.nx, p.ny = w["nx"], w["ny"]
+    p.batch = batch if batch is not None else w.get("batch", 1)
+    p.prec = HOM_C128 if w.get("prec", "c128") == "c128" else HOM_C64
+    p.dx, p.dy = w["dx"], w["dy"]
+    p.B, p.omega_y = w["B"], w["omega"]
+    p.dt = w["dt"] if dt is None else dt
+    p.qpc_h, p.qpc_w, p.qpc_x0 = w["qpc_h"], w["qpc_w"], w.get("qpc_x0", 0.0)
+    p.coul_lambda, p.coul_soft = w["lam"], w["soft"]
+    p.observe_every = w.get("observe_every", 0)
+    p.ckpt_slots = ckpt_slots
+    return p
+
+
+def make_packet(d: dict) -> hom_packet:
+    pk = hom_packet()
+    pk.x0, pk.sigma, pk.energy, pk.k0 = d["x0"], d["sigma"], d.get("energy", 0.0), d.get("k0", 0.0)
+    pk.dir, pk.by_k0 = d.get("dir", 1), 1 if d.get("by_k0", False) else 0
+    return pk
+
+
+class Propagator:
+    """Device state + workspace (PyTorch tensors) and a libhom context.
+
+    ``w`` is a workload description (see ``workloads``): grid, time step,
+    default potential, and a list ``sims`` of per-simulation QPC / Coulomb
+    parameters and packets.  The state is initialised from the packets
+    unless ``init=False``.
+    """
+
+    def __init__(self, w: dict, device: str = "cuda", ckpt_slots: int = 0, init: bool = True, stream=None):
+        import torch
+
+        self.w = w
+        self.batch = len(w["sims"]) if "sims" in w else w.get("batch", 1)
+        self.params = make_params(w, self.batch, ckpt_slots)
+        sb = hom_state_bytes(self.params)
+        wb = hom_workspace_bytes(self.params)
+        if sb == 0 or wb == 0:
+            raise HomError(HOM_ERR_ARG, "invalid parameters")
+        self.dtype = torch.complex128 if self.params.prec == HOM_C128 else torch.complex64
+        self.np_dtype = np.complex128 if self.params.prec == HOM_C128 else np.complex64
+        n = w["nx"] * w["ny"]
+        self.n = n
+        self.device = torch.device(device)
+        self.state = torch.empty((self.batch, n, n), dtype=self.dtype, device=self.device)
+        self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = hom_create(self.params, self.state.data_ptr(), self.workspace.data_ptr(), wb,
+                              self.stream.cuda_stream)
+        if "sims" in w:
+            for b, s in enumerate(w["sims"]):
+                hom_set_sim_params(self.ctx, b, s["qpc_h"], s["qpc_w"], s["lam"])
+                if init:
+                    hom_init_packets(self.ctx, b, make_packet(s["alpha"]), make_packet(s["beta"]), s["exch"])
+
+    def step(self, nsteps: int):
+        hom_step(self.ctx, nsteps)
+
+    def observables(self) -> list[dict]:
+        return hom_observables(self.ctx, self.batch)
+
+    def backward(self, nsteps: int, K: int):
+        return hom_backward(self.ctx, self.batch, nsteps, K)
+
+    def get_state(self, b: int = 0) -> np.ndarray:
+        nx, ny = self.w["nx"], self.w["ny"]
+        out = np.empty((nx, ny, nx, ny), dtype=self.np_dtype)
+        hom_copy_state(self.ctx, b, out, to_device=False)
+        return out
+
+    def set_state(self, b: int, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, dtype=self.np_dtype)
+        hom_copy_state(self.ctx, b, a, to_device=True)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            hom_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

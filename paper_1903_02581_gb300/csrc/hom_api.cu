@@ -1,0 +1,715 @@
+// hom_api.cu -- the C ABI of libhom (declared in include/hom.h): parameter
+// checks, FP64 construction of the phase tables and of the edge packets,
+// workspace layout, and the launch sequence of a Strang step.
+//
+// Paper: arXiv:1903.02581, Sec. II.C (Eq. evoloperat, Landau-gauge
+// Hamiltonian), Appendix A (Eq. 2PTB), Eq. coulomb, Eq. twopstate,
+// Eq. singlepwp, Eq. p_bunching.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hom.h"
+#include "hom_internal.h"
+
+namespace {
+
+using cd = std::complex<double>;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+size_t elem_bytes(const hom_params& p) { return p.prec == HOM_C128 ? 16 : 8; }
+
+// e^{-i theta} - 1 with theta reduced modulo 2 pi in FP64 before the sine;
+// the real part is formed as -2 sin^2(theta/2), exact to rounding even when
+// theta is small (the tables hold this deviation from 1, see apply_delta).
+cd phase_delta(double theta) {
+  const double t = std::remainder(theta, kTwoPi);
+  const double h = std::sin(0.5 * t);
+  return cd(-2.0 * h * h, -std::sin(t));
+}
+
+// Frequency index held at position p after the forward transform of an axis
+// of length n (digit-transposed for n > 16, natural otherwise).
+int freq_at(int n, int p) {
+  if (n <= 16) return p;
+  const int n1 = n >= 128 ? 16 : 8, n2 = n / n1;
+  return p / n2 + n1 * (p % n2);
+}
+
+double wavenumber(int n, double d, int m) {
+  const int s = m < n / 2 ? m : m - n;
+  return kTwoPi * s / (n * d);
+}
+
+double coord(int n, double d, int j) { return (j - 0.5 * (n - 1)) * d; }
+
+struct SimParams {
+  double h, w, lam;
+};
+
+// Workspace layout: byte offsets of every region.
+struct Layout {
+  size_t qa[2], qt[2], gy[2], twx, twy;   // [0] = +dt, [1] = -dt
+  size_t p1h[2], p1f[2], p12h[2], p12f[2];
+  size_t tx, ty, v1, v12;
+  size_t part_row, part_col, obs;
+  size_t packets, dbeta, coef, exch, scratch;
+  size_t ckpt;
+  size_t total;
+  int tiles_row, tiles_col;
+};
+
+bool sizes_ok(const hom_params& p, std::string* why) {
+  char buf[256];
+  if (!pow2_in(p.nx, 16, 256) || !pow2_in(p.ny, 16, 64)) {
+    snprintf(buf, sizeof buf, "nx must be a power of two in [16,256] and ny in [16,64] (got %d, %d)", p.nx, p.ny);
+    if (why) *why = buf;
+    return false;
+  }
+  if (p.prec != HOM_C64 && p.prec != HOM_C128) {
+    if (why) *why = "prec must be HOM_C64 or HOM_C128";
+    return false;
+  }
+  if (p.prec == HOM_C128 && p.nx * p.ny > 8192) {
+    if (why) *why = "complex128 needs nx*ny <= 8192 (one plane in shared memory)";
+    return false;
+  }
+  if (p.batch < 1) {
+    if (why) *why = "batch must be >= 1";
+    return false;
+  }
+  if (!(p.dx > 0) || !(p.dy > 0) || !std::isfinite(p.dx) || !std::isfinite(p.dy)) {
+    if (why) *why = "dx and dy must be positive";
+    return false;
+  }
+  if (!std::isfinite(p.dt) || p.dt == 0.0) {
+    if (why) *why = "dt must be finite and non-zero";
+    return false;
+  }
+  if (!(p.coul_soft > 0) || !std::isfinite(p.B) || !std::isfinite(p.omega_y) || !(p.qpc_w > 0) ||
+      !std::isfinite(p.qpc_h) || !std::isfinite(p.coul_lambda) || !std::isfinite(p.qpc_x0)) {
+    if (why) *why = "coul_soft and qpc_w must be positive; B, omega_y, qpc_h, qpc_x0, coul_lambda finite";
+    return false;
+  }
+  if (p.ckpt_slots < 0) {
+    if (why) *why = "ckpt_slots must be >= 0";
+    return false;
+  }
+  return true;
+}
+
+int tiles_of(const hom_params& p, bool col) {
+  hom::GeoInfo g = p.prec == HOM_C128 ? hom::geo_info<double>(p.nx, p.ny, col) : hom::geo_info<float>(p.nx, p.ny, col);
+  return g.G > 0 ? g.tiles_per_sim : 0;
+}
+
+Layout make_layout(const hom_params& p) {
+  Layout L{};
+  const size_t eb = elem_bytes(p);
+  const size_t n = (size_t)p.nx * p.ny;
+  const size_t D = (size_t)(2 * p.nx - 1) * (2 * p.ny - 1);
+  const size_t B = (size_t)p.batch;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  for (int s = 0; s < 2; ++s) {
+    L.qa[s] = take(n * eb);
+    L.qt[s] = take(n * eb);
+    L.gy[s] = take(p.ny * eb);
+    L.p1h[s] = take(B * n * eb);
+    L.p1f[s] = take(B * n * eb);
+    L.p12h[s] = take(B * D * eb);
+    L.p12f[s] = take(B * D * eb);
+  }
+  L.twx = take(2 * p.nx * eb);
+  L.twy = take(2 * p.ny * eb);
+  L.tx = take(n * 8);
+  L.ty = take(p.ny * 8);
+  L.v1 = take(B * n * 8);
+  L.v12 = take(B * D * 8);
+  L.tiles_row = tiles_of(p, false);
+  L.tiles_col = tiles_of(p, true);
+  L.part_row = take(B * L.tiles_row * hom::NPART * 8);
+  L.part_col = take(B * L.tiles_col * hom::NPART * 8);
+  L.obs = take(2 * B * hom::NPART * 8);
+  L.packets = take(B * 2 * n * 16);
+  L.dbeta = take(B * n * 16);
+  L.coef = take(B * 8);
+  L.exch = take(B * 4);
+  L.scratch = take(B * 8 * 8);
+  L.ckpt = take((size_t)p.ckpt_slots * B * n * n * eb);
+  L.total = o;
+  return L;
+}
+
+std::string g_create_error = "no error";
+
+}  // namespace
+
+struct hom_ctx {
+  hom_params p;
+  char* state;
+  char* ws;
+  cudaStream_t stream;
+  int device;
+  Layout L;
+  std::vector<SimParams> sims;
+  std::vector<int> have_packets;    // packets set by hom_init_packets
+  std::vector<int> exch;
+  std::string err;
+  bool poisoned;
+  // instrumentation (hom_profile)
+  bool prof;
+  std::vector<cudaEvent_t> ev;     // event pool
+  std::vector<int> ev_kind;        // per recorded pair: 0 row, 1 col
+  size_t ev_used;
+  double prof_ms[2];
+  long long prof_n[2];
+};
+
+namespace {
+
+hom_status fail(hom_ctx* c, hom_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (s == HOM_ERR_CUDA || s == HOM_ERR_TIMEOUT) c->poisoned = true;
+  } else {
+    g_create_error = buf;
+  }
+  return s;
+}
+
+#define HOM_CUDA(ctx, call)                                                                          \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return fail((ctx), HOM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+hom_status enter(hom_ctx* c) {
+  if (!c) return HOM_ERR_ARG;
+  if (c->poisoned) {
+    return HOM_ERR_STATE;
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return fail(c, HOM_ERR_CUDA, "cudaSetDevice failed: %s", cudaGetErrorString(e));
+  return HOM_OK;
+}
+
+template <typename C>
+void store_complex(std::vector<unsigned char>& buf, size_t i, cd v) {
+  using R = decltype(C{}.x);
+  C c{(R)v.real(), (R)v.imag()};
+  std::memcpy(buf.data() + i * sizeof(C), &c, sizeof(C));
+}
+
+void put(std::vector<unsigned char>& buf, bool dbl, size_t i, cd v) {
+  if (dbl) store_complex<double2>(buf, i, v);
+  else store_complex<float2>(buf, i, v);
+}
+
+hom_status upload(hom_ctx* c, size_t off, const void* src, size_t bytes) {
+  HOM_CUDA(c, cudaMemcpyAsync(c->ws + off, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  return HOM_OK;
+}
+
+// Tables shared by all simulations: kinetic phases (both signs of dt),
+// twiddles, kinetic weights of the observables.
+hom_status build_shared_tables(hom_ctx* c) {
+  const hom_params& p = c->p;
+  const bool dbl = p.prec == HOM_C128;
+  const size_t eb = elem_bytes(p);
+  const int nx = p.nx, ny = p.ny, n = nx * ny;
+  std::vector<unsigned char> qa(n * eb), qt(n * eb), gy(ny * eb), twx(2 * nx * eb), twy(2 * ny * eb);
+  std::vector<double> tx(n), ty(ny);
+  for (int sgn = 0; sgn < 2; ++sgn) {
+    const double dt = sgn == 0 ? p.dt : -p.dt;
+    for (int px = 0; px < nx; ++px) {
+      const double k = wavenumber(nx, p.dx, freq_at(nx, px));
+      for (int j = 0; j < ny; ++j) {
+        const double y = coord(ny, p.dy, j);
+        const double t = 0.5 * (k - p.B * y) * (k - p.B * y);
+        const cd q = phase_delta(0.5 * dt * t);      // e^{-i (dt/2) T_x} - 1
+        put(qa, dbl, (size_t)px * ny + j, q);
+        put(qt, dbl, (size_t)j * nx + px, q);
+        if (sgn == 0) tx[(size_t)px * ny + j] = t;
+      }
+    }
+    for (int py = 0; py < ny; ++py) {
+      const double k = wavenumber(ny, p.dy, freq_at(ny, py));
+      put(gy, dbl, py, phase_delta(dt * 0.5 * k * k));       // e^{-i dt T_y} - 1
+      if (sgn == 0) ty[py] = 0.5 * k * k;
+    }
+    hom_status s;
+    if ((s = upload(c, c->L.qa[sgn], qa.data(), qa.size())) != HOM_OK) return s;
+    if ((s = upload(c, c->L.qt[sgn], qt.data(), qt.size())) != HOM_OK) return s;
+    if ((s = upload(c, c->L.gy[sgn], gy.data(), gy.size())) != HOM_OK) return s;
+    HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  // twiddles e^{-2 pi i j / n} as hi parts then lo parts (lo = 0 in FP64)
+  auto twiddles = [&](std::vector<unsigned char>& buf, int nn) {
+    for (int j = 0; j < nn; ++j) {
+      const double a = kTwoPi * j / nn;
+      const cd w(std::cos(a), -std::sin(a));
+      const cd hi = dbl ? w : cd((float)w.real(), (float)w.imag());
+      put(buf, dbl, j, hi);
+      put(buf, dbl, nn + j, dbl ? cd(0, 0) : w - hi);
+    }
+  };
+  twiddles(twx, nx);
+  twiddles(twy, ny);
+  hom_status s;
+  if ((s = upload(c, c->L.twx, twx.data(), twx.size())) != HOM_OK) return s;
+  if ((s = upload(c, c->L.twy, twy.data(), twy.size())) != HOM_OK) return s;
+  if ((s = upload(c, c->L.tx, tx.data(), tx.size() * 8)) != HOM_OK) return s;
+  if ((s = upload(c, c->L.ty, ty.data(), ty.size() * 8)) != HOM_OK) return s;
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+// Per-simulation potential tables: e^{-i tau V1}, e^{-i tau V12} for
+// tau = +-dt/2, +-dt, and the real V1, V12 for the observables.
+hom_status build_sim_tables(hom_ctx* c, int b) {
+  const hom_params& p = c->p;
+  const SimParams& sp = c->sims[b];
+  const bool dbl = p.prec == HOM_C128;
+  const size_t eb = elem_bytes(p);
+  const int nx = p.nx, ny = p.ny, n = nx * ny;
+  const int dny = 2 * ny - 1;
+  const size_t D = (size_t)(2 * nx - 1) * dny;
+  std::vector<double> v1(n), v12(D);
+  for (int ix = 0; ix < nx; ++ix) {
+    const double x = coord(nx, p.dx, ix);
+    const double g = std::exp(-(x - p.qpc_x0) * (x - p.qpc_x0) / (2.0 * sp.w * sp.w));
+    for (int iy = 0; iy < ny; ++iy) {
+      const double y = coord(ny, p.dy, iy);
+      v1[(size_t)ix * ny + iy] = 0.5 * p.omega_y * p.omega_y * y * y + sp.h * g;
+    }
+  }
+  for (int ddx = -(nx - 1); ddx <= nx - 1; ++ddx) {
+    for (int ddy = -(ny - 1); ddy <= ny - 1; ++ddy) {
+      const double rx = ddx * p.dx, ry = ddy * p.dy;
+      v12[(size_t)(ddx + nx - 1) * dny + (ddy + ny - 1)] =
+          sp.lam / std::sqrt(rx * rx + ry * ry + p.coul_soft * p.coul_soft);
+    }
+  }
+  std::vector<unsigned char> t1(n * eb), t12(D * eb);
+  for (int sgn = 0; sgn < 2; ++sgn) {
+    const double dt = sgn == 0 ? p.dt : -p.dt;
+    for (int half = 0; half < 2; ++half) {
+      const double tau = half ? 0.5 * dt : dt;
+      for (int i = 0; i < n; ++i) put(t1, dbl, i, phase_delta(tau * v1[i]));
+      for (size_t i = 0; i < D; ++i) put(t12, dbl, i, phase_delta(tau * v12[i]));
+      const size_t o1 = (half ? c->L.p1h[sgn] : c->L.p1f[sgn]) + (size_t)b * n * eb;
+      const size_t o12 = (half ? c->L.p12h[sgn] : c->L.p12f[sgn]) + (size_t)b * D * eb;
+      hom_status s;
+      if ((s = upload(c, o1, t1.data(), t1.size())) != HOM_OK) return s;
+      if ((s = upload(c, o12, t12.data(), t12.size())) != HOM_OK) return s;
+      HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  hom_status s;
+  if ((s = upload(c, c->L.v1 + (size_t)b * n * 8, v1.data(), n * 8)) != HOM_OK) return s;
+  if ((s = upload(c, c->L.v12 + (size_t)b * D * 8, v12.data(), D * 8)) != HOM_OK) return s;
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+// Edge packet of Eq. (singlepwp): sum over the grid wavenumbers k of
+// e^{-sigma^2 (k-k0)^2} e^{i k (x - x0)} phi_k(y), phi_k the lowest hybrid
+// level of the parabolic edge, (Omega/pi)^{1/4} e^{-Omega (y - k B/Omega^2)^2 / 2},
+// Omega^2 = B^2 + omega^2; normalised so that sum |psi|^2 dx dy = 1.  With
+// dpsi != nullptr also returns d psi / d x0 (the norm does not depend on x0).
+hom_status build_packet(hom_ctx* c, const hom_packet& pk, std::vector<cd>& psi, std::vector<cd>* dpsi) {
+  const hom_params& p = c->p;
+  const int nx = p.nx, ny = p.ny;
+  const double Om = std::sqrt(p.B * p.B + p.omega_y * p.omega_y);
+  if (!std::isfinite(pk.x0) || !(pk.sigma > 0) || !std::isfinite(pk.sigma))
+    return fail(c, HOM_ERR_ARG, "packet needs finite x0 and sigma > 0");
+  if (Om <= 0) return fail(c, HOM_ERR_ARG, "packets need B != 0 or omega_y != 0");
+  double k0;
+  if (pk.by_k0) {
+    if (!std::isfinite(pk.k0)) return fail(c, HOM_ERR_ARG, "k0 must be finite");
+    k0 = pk.k0;
+  } else {
+    if (!(p.omega_y > 0)) return fail(c, HOM_ERR_ARG, "an energy needs omega_y > 0 (or give k0 with by_k0)");
+    if (!(pk.energy >= 0.5 * Om) || !std::isfinite(pk.energy))
+      return fail(c, HOM_ERR_ARG, "energy %g below the lowest hybrid level %g", pk.energy, 0.5 * Om);
+    if (pk.dir != 1 && pk.dir != -1) return fail(c, HOM_ERR_ARG, "dir must be +1 or -1");
+    k0 = pk.dir * Om * std::sqrt(2.0 * (pk.energy - 0.5 * Om)) / p.omega_y;
+  }
+  psi.assign((size_t)nx * ny, cd(0, 0));
+  if (dpsi) dpsi->assign((size_t)nx * ny, cd(0, 0));
+  std::vector<double> chi(ny);
+  for (int m = 0; m < nx; ++m) {
+    const double k = wavenumber(nx, p.dx, m);
+    const double wk = std::exp(-pk.sigma * pk.sigma * (k - k0) * (k - k0));
+    if (wk < 1e-300) continue;
+    const double yk = k * p.B / (Om * Om);
+    for (int j = 0; j < ny; ++j) {
+      const double y = coord(ny, p.dy, j) - yk;
+      chi[j] = std::pow(Om / kPi, 0.25) * std::exp(-0.5 * Om * y * y);
+    }
+    for (int ix = 0; ix < nx; ++ix) {
+      const double arg = std::fmod(k * (coord(nx, p.dx, ix) - pk.x0), kTwoPi);
+      const cd e = wk * cd(std::cos(arg), std::sin(arg));
+      for (int j = 0; j < ny; ++j) {
+        psi[(size_t)ix * ny + j] += e * chi[j];
+        if (dpsi) (*dpsi)[(size_t)ix * ny + j] += cd(0, -k) * e * chi[j];
+      }
+    }
+  }
+  double s = 0;
+  for (const cd& v : psi) s += std::norm(v);
+  s *= p.dx * p.dy;
+  if (!(s > 0)) return fail(c, HOM_ERR_ARG, "packet has zero norm on this grid");
+  const double inv = 1.0 / std::sqrt(s);
+  for (cd& v : psi) v *= inv;
+  if (dpsi)
+    for (cd& v : *dpsi) v *= inv;
+  return HOM_OK;
+}
+
+constexpr size_t kEventPool = 4096;
+
+// Sum the elapsed times of the recorded event pairs (the stream is synchronised).
+hom_status harvest_events(hom_ctx* c) {
+  if (c->ev_used == 0) return HOM_OK;
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    HOM_CUDA(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    const int k = c->ev_kind[i / 2];
+    c->prof_ms[k] += ms;
+    c->prof_n[k] += 1;
+  }
+  c->ev_used = 0;
+  c->ev_kind.clear();
+  return HOM_OK;
+}
+
+hom_status prof_begin(hom_ctx* c, size_t* idx) {
+  if (c->ev_used + 2 > c->ev.size()) {
+    hom_status s = harvest_events(c);
+    if (s != HOM_OK) return s;
+  }
+  *idx = c->ev_used;
+  HOM_CUDA(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
+  return HOM_OK;
+}
+
+hom_status prof_end(hom_ctx* c, size_t idx, int kind) {
+  HOM_CUDA(c, cudaEventRecord(c->ev[idx + 1], c->stream));
+  c->ev_used = idx + 2;
+  c->ev_kind.push_back(kind);
+  return HOM_OK;
+}
+
+template <typename T>
+hom_status step_sequence(hom_ctx* c, int nsteps, int sgn) {
+  using C = typename hom::Cx<T>::type;
+  const hom_params& p = c->p;
+  hom::PassArgs<C> a{};
+  a.psi = reinterpret_cast<C*>(c->state);
+  a.qa = reinterpret_cast<const C*>(c->ws + c->L.qa[sgn]);
+  a.qt = reinterpret_cast<const C*>(c->ws + c->L.qt[sgn]);
+  a.gy = reinterpret_cast<const C*>(c->ws + c->L.gy[sgn]);
+  a.twx = reinterpret_cast<const C*>(c->ws + c->L.twx);
+  a.twy = reinterpret_cast<const C*>(c->ws + c->L.twy);
+  const C* p1h = reinterpret_cast<const C*>(c->ws + c->L.p1h[sgn]);
+  const C* p1f = reinterpret_cast<const C*>(c->ws + c->L.p1f[sgn]);
+  const C* p12h = reinterpret_cast<const C*>(c->ws + c->L.p12h[sgn]);
+  const C* p12f = reinterpret_cast<const C*>(c->ws + c->L.p12f[sgn]);
+  for (int s = 0; s < nsteps; ++s) {
+    size_t ev = 0;
+    hom_status st;
+    a.apply_v = 1;
+    a.p1 = s == 0 ? p1h : p1f;
+    a.p12 = s == 0 ? p12h : p12f;
+    if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, false, a, p.batch, c->stream)));
+    if (c->prof && (st = prof_end(c, ev, 0)) != HOM_OK) return st;
+    a.apply_v = s == nsteps - 1;
+    a.p1 = p1h;
+    a.p12 = p12h;
+    if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, true, a, p.batch, c->stream)));
+    if (c->prof && (st = prof_end(c, ev, 1)) != HOM_OK) return st;
+  }
+  return HOM_OK;
+}
+
+hom_status run_steps(hom_ctx* c, int nsteps, int sgn) {
+  return c->p.prec == HOM_C128 ? step_sequence<double>(c, nsteps, sgn) : step_sequence<float>(c, nsteps, sgn);
+}
+
+template <typename T>
+hom_status measure_launch(hom_ctx* c) {
+  using C = typename hom::Cx<T>::type;
+  const hom_params& p = c->p;
+  hom::MeasureArgs<C> m{};
+  m.psi = reinterpret_cast<const C*>(c->state);
+  m.twx = reinterpret_cast<const C*>(c->ws + c->L.twx);
+  m.twy = reinterpret_cast<const C*>(c->ws + c->L.twy);
+  m.tx = reinterpret_cast<const double*>(c->ws + c->L.tx);
+  m.ty = reinterpret_cast<const double*>(c->ws + c->L.ty);
+  m.v1 = reinterpret_cast<const double*>(c->ws + c->L.v1);
+  m.v12 = reinterpret_cast<const double*>(c->ws + c->L.v12);
+  double* obs = reinterpret_cast<double*>(c->ws + c->L.obs);
+  m.partial = reinterpret_cast<double*>(c->ws + c->L.part_row);
+  HOM_CUDA(c, (hom::launch_measure<T>(p.nx, p.ny, false, m, p.batch, c->stream)));
+  HOM_CUDA(c, hom::launch_reduce(m.partial, c->L.tiles_row, p.batch, obs, c->stream));
+  m.partial = reinterpret_cast<double*>(c->ws + c->L.part_col);
+  HOM_CUDA(c, (hom::launch_measure<T>(p.nx, p.ny, true, m, p.batch, c->stream)));
+  HOM_CUDA(c, hom::launch_reduce(m.partial, c->L.tiles_col, p.batch, obs + (size_t)p.batch * hom::NPART, c->stream));
+  return HOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hom_state_bytes(const hom_params* p) {
+  if (!p || !sizes_ok(*p, nullptr)) return 0;
+  const size_t n = (size_t)p->nx * p->ny;
+  return (size_t)p->batch * n * n * elem_bytes(*p);
+}
+
+size_t hom_workspace_bytes(const hom_params* p) {
+  if (!p || !sizes_ok(*p, nullptr)) return 0;
+  return make_layout(*p).total;
+}
+
+hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, size_t workspace_bytes,
+                      void* cuda_stream, hom_ctx** out) {
+  if (!out) return fail(nullptr, HOM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, HOM_ERR_ARG, "params is NULL");
+  std::string why;
+  if (!sizes_ok(*p, &why)) return fail(nullptr, HOM_ERR_ARG, "%s", why.c_str());
+  if (!d_state || !d_workspace) return fail(nullptr, HOM_ERR_ARG, "state and workspace pointers must be non-NULL");
+  if (((uintptr_t)d_state % kAlign) || ((uintptr_t)d_workspace % kAlign))
+    return fail(nullptr, HOM_ERR_ARG, "state and workspace must be %zu-byte aligned", kAlign);
+  const Layout L = make_layout(*p);
+  if (workspace_bytes < L.total)
+    return fail(nullptr, HOM_ERR_NOMEM, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
+                L.total);
+  if (L.tiles_row <= 0 || L.tiles_col <= 0) return fail(nullptr, HOM_ERR_ARG, "unsupported grid");
+  hom_ctx* c = new (std::nothrow) hom_ctx();
+  if (!c) return fail(nullptr, HOM_ERR_NOMEM, "host allocation failed");
+  c->p = *p;
+  c->state = static_cast<char*>(d_state);
+  c->ws = static_cast<char*>(d_workspace);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->L = L;
+  c->poisoned = false;
+  c->err = "no error";
+  c->prof = false;
+  c->ev_used = 0;
+  c->prof_ms[0] = c->prof_ms[1] = 0.0;
+  c->prof_n[0] = c->prof_n[1] = 0;
+  c->sims.assign(p->batch, SimParams{p->qpc_h, p->qpc_w, p->coul_lambda});
+  c->have_packets.assign(p->batch, 0);
+  c->exch.assign(p->batch, -1);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, HOM_ERR_CUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+  }
+  hom_status s = build_shared_tables(c);
+  for (int b = 0; s == HOM_OK && b < p->batch; ++b) s = build_sim_tables(c, b);
+  if (s != HOM_OK) {
+    g_create_error = c->err;
+    delete c;
+    return s;
+  }
+  *out = c;
+  return HOM_OK;
+}
+
+hom_status hom_set_sim_params(hom_ctx* c, int32_t b, double qpc_h, double qpc_w, double coul_lambda) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (b < 0 || b >= c->p.batch) return fail(c, HOM_ERR_ARG, "simulation index %d out of range", b);
+  if (!std::isfinite(qpc_h) || !(qpc_w > 0) || !std::isfinite(qpc_w) || !std::isfinite(coul_lambda))
+    return fail(c, HOM_ERR_ARG, "qpc_h, coul_lambda finite and qpc_w > 0 required");
+  c->sims[b] = SimParams{qpc_h, qpc_w, coul_lambda};
+  return build_sim_tables(c, b);
+}
+
+hom_status hom_init_packets(hom_ctx* c, int32_t b, const hom_packet* alpha, const hom_packet* beta, int32_t exch) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  const hom_params& p = c->p;
+  if (!alpha || !beta) return fail(c, HOM_ERR_ARG, "packets must be non-NULL");
+  if (b < -1 || b >= p.batch) return fail(c, HOM_ERR_ARG, "simulation index %d out of range", b);
+  if (exch < -1 || exch > 1) return fail(c, HOM_ERR_ARG, "exch must be -1, 0 or +1");
+  std::vector<cd> a, be, dbe;
+  if ((s = build_packet(c, *alpha, a, nullptr)) != HOM_OK) return s;
+  if ((s = build_packet(c, *beta, be, &dbe)) != HOM_OK) return s;
+  const size_t n = (size_t)p.nx * p.ny;
+  // sum over r1, r2 of |a(r1) b(r2) + s b(r1) a(r2)|^2 = 2 |a|^2 |b|^2 + 2 s |<a|b>|^2  (s = +-1)
+  double na = 0, nb = 0;
+  cd ab(0, 0);
+  for (size_t i = 0; i < n; ++i) {
+    na += std::norm(a[i]);
+    nb += std::norm(be[i]);
+    ab += std::conj(a[i]) * be[i];
+  }
+  const double sum = exch == 0 ? na * nb : 2.0 * na * nb + 2.0 * exch * std::norm(ab);
+  const double dV = p.dx * p.dx * p.dy * p.dy;
+  if (!(sum > 1e-12 * na * nb) || !(sum * dV > 1e-300))
+    return fail(c, HOM_ERR_ARG, "the combined state vanishes (identical packets?)");
+  const double coef = 1.0 / std::sqrt(sum * dV);
+  const int b0 = b < 0 ? 0 : b, b1 = b < 0 ? p.batch : b + 1;
+  std::vector<double2> host(2 * n), dhost(n);
+  for (size_t i = 0; i < n; ++i) {
+    host[i] = double2{a[i].real(), a[i].imag()};
+    host[n + i] = double2{be[i].real(), be[i].imag()};
+    dhost[i] = double2{dbe[i].real(), dbe[i].imag()};
+  }
+  for (int bb = b0; bb < b1; ++bb) {
+    if ((s = upload(c, c->L.packets + (size_t)bb * 2 * n * 16, host.data(), 2 * n * 16)) != HOM_OK) return s;
+    if ((s = upload(c, c->L.dbeta + (size_t)bb * n * 16, dhost.data(), n * 16)) != HOM_OK) return s;
+    if ((s = upload(c, c->L.coef + (size_t)bb * 8, &coef, 8)) != HOM_OK) return s;
+    if ((s = upload(c, c->L.exch + (size_t)bb * 4, &exch, 4)) != HOM_OK) return s;
+    c->have_packets[bb] = 1;
+    c->exch[bb] = exch;
+  }
+  const double2* pk = reinterpret_cast<const double2*>(c->ws + c->L.packets);
+  const double* cf = reinterpret_cast<const double*>(c->ws + c->L.coef);
+  const int* ex = reinterpret_cast<const int*>(c->ws + c->L.exch);
+  if (p.prec == HOM_C128)
+    HOM_CUDA(c, hom::launch_slater<double>(c->state, pk, cf, ex, b0, b1 - b0, (int)n, c->stream));
+  else
+    HOM_CUDA(c, hom::launch_slater<float>(c->state, pk, cf, ex, b0, b1 - b0, (int)n, c->stream));
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+hom_status hom_step(hom_ctx* c, int32_t nsteps) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (nsteps < 0) return fail(c, HOM_ERR_ARG, "nsteps must be >= 0");
+  return run_steps(c, nsteps, 0);
+}
+
+hom_status hom_observables(hom_ctx* c, hom_obs* out) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (!out) return fail(c, HOM_ERR_ARG, "out is NULL");
+  const hom_params& p = c->p;
+  s = p.prec == HOM_C128 ? measure_launch<double>(c) : measure_launch<float>(c);
+  if (s != HOM_OK) return s;
+  std::vector<double> h(2 * (size_t)p.batch * hom::NPART);
+  HOM_CUDA(c, cudaMemcpyAsync(h.data(), c->ws + c->L.obs, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double dV = p.dx * p.dx * p.dy * p.dy;
+  for (int b = 0; b < p.batch; ++b) {
+    const double* r = &h[(size_t)b * hom::NPART];
+    const double* q = &h[((size_t)p.batch + b) * hom::NPART];
+    hom_obs o;
+    o.norm = r[0] * dV;
+    o.e_pot = r[1] * dV;
+    o.e_coul = r[2] * dV;
+    o.p_bunch = r[3] * dV;
+    o.e_kin = dV * ((r[4] + q[4]) / p.nx + (r[5] + q[5]) / ((double)p.nx * p.ny));
+    o.energy = o.e_kin + o.e_pot + o.e_coul;
+    out[b] = o;
+    if (!std::isfinite(o.norm) || !std::isfinite(o.energy))
+      return fail(c, HOM_ERR_NUMERIC, "non-finite observables in simulation %d", b);
+  }
+  return HOM_OK;
+}
+
+hom_status hom_backward(hom_ctx* c, int32_t nsteps, int32_t K, double* loss, double* grad) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  (void)nsteps;
+  (void)K;
+  (void)loss;
+  (void)grad;
+  return fail(c, HOM_ERR_STATE, "hom_backward is not available in this build");
+}
+
+hom_status hom_copy_state(hom_ctx* c, int32_t b, void* host, size_t bytes, int32_t to_device) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  const hom_params& p = c->p;
+  if (b < 0 || b >= p.batch) return fail(c, HOM_ERR_ARG, "simulation index %d out of range", b);
+  const size_t n = (size_t)p.nx * p.ny;
+  const size_t per = n * n * elem_bytes(p);
+  if (!host || bytes != per) return fail(c, HOM_ERR_ARG, "host buffer must hold exactly %zu bytes", per);
+  char* dev = c->state + (size_t)b * per;
+  if (to_device) {
+    HOM_CUDA(c, cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, c->stream));
+    c->have_packets[b] = 0;
+  } else {
+    HOM_CUDA(c, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  }
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+const char* hom_last_error(const hom_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+hom_status hom_profile(hom_ctx* c, int32_t enable) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (enable && c->ev.empty()) {
+    c->ev.resize(kEventPool, nullptr);
+    for (auto& e : c->ev) HOM_CUDA(c, cudaEventCreate(&e));
+  }
+  if (enable) {
+    HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->ev_used = 0;
+    c->ev_kind.clear();
+    c->prof_ms[0] = c->prof_ms[1] = 0.0;
+    c->prof_n[0] = c->prof_n[1] = 0;
+  }
+  c->prof = enable != 0;
+  return HOM_OK;
+}
+
+hom_status hom_profile_read(hom_ctx* c, double* ms_row, double* ms_col, int64_t* n_row, int64_t* n_col) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if ((s = harvest_events(c)) != HOM_OK) return s;
+  if (ms_row) *ms_row = c->prof_ms[0];
+  if (ms_col) *ms_col = c->prof_ms[1];
+  if (n_row) *n_row = c->prof_n[0];
+  if (n_col) *n_col = c->prof_n[1];
+  return HOM_OK;
+}
+
+void hom_destroy(hom_ctx* c) {
+  if (!c) return;
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

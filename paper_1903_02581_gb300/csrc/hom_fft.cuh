@@ -1,0 +1,151 @@
+// hom_fft.cuh -- complex arithmetic and in-register DFTs for libhom kernels.
+//
+// The 2D Fourier transforms F_{x1,x2} and F_{y1,y2} of Eq. (evoloperat) of
+// arXiv:1903.02581 are applied here one particle at a time as 1D DFTs along
+// each axis (F_{x1,x2} = F_{x1} F_{x2}).  A line of length N <= 16 is
+// transformed entirely in registers; longer lines are split N = N1 * N2 into
+// two register passes with a twiddle between them (Cooley-Tukey), the second
+// pass leaving the coefficients in digit-transposed order, which the phase
+// tables and the inverse transform consume directly.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hom {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+template <typename C> struct Re;
+template <> struct Re<float2> { using type = float; };
+template <> struct Re<double2> { using type = double; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C> __device__ __forceinline__ typename Re<C>::type cnorm2(C a) {
+  return a.x * a.x + a.y * a.y;
+}
+template <typename C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
+
+// cos and sin of 2*pi*j/16, j = 0..15 (exact values of the 16th roots of unity).
+__device__ __forceinline__ constexpr double cos16(int j) {
+  switch (j & 15) {
+    case 0: return 1.0;
+    case 1: case 15: return 0.92387953251128675613;   // cos(pi/8)
+    case 2: case 14: return 0.70710678118654752440;   // cos(pi/4)
+    case 3: case 13: return 0.38268343236508977173;   // cos(3pi/8)
+    case 4: case 12: return 0.0;
+    case 5: case 11: return -0.38268343236508977173;
+    case 6: case 10: return -0.70710678118654752440;
+    case 7: case 9: return -0.92387953251128675613;
+    default: return -1.0;
+  }
+}
+__device__ __forceinline__ constexpr double sin16(int j) { return cos16(j + 12); }
+
+// v * (1 + d): a unit-modulus phase stored as its deviation d = w - 1 from 1.
+// For the small phase angles of a split step, d carries the phase with full
+// relative precision, so the rounded table has |1 + d| = 1 to far better than
+// the precision of w itself; the product costs the same four FMAs.
+template <typename C>
+__device__ __forceinline__ C apply_delta(C v, C d) {
+  return C{fma(v.x, d.x, fma(-v.y, d.y, v.x)), fma(v.x, d.y, fma(v.y, d.x, v.y))};
+}
+
+// v * (hi + lo) (or v * conj(hi + lo)): a twiddle carried as an unevaluated
+// sum of two values, so that its modulus is 1 to twice the working precision.
+// Rounding a unit twiddle to one FP32 value leaves |w| != 1 by up to 6e-8,
+// with the same sign every step: an energy drift the compensated product
+// removes.  In FP64 the low part is not used.
+template <bool CONJ, typename C>
+__device__ __forceinline__ C cmul_hl(C v, C hi, C lo) {
+  using R = typename Re<C>::type;
+  const R hy = CONJ ? -hi.y : hi.y;
+  if constexpr (sizeof(R) == 8) {
+    return C{v.x * hi.x - v.y * hy, v.x * hy + v.y * hi.x};
+  } else {
+    const R ly = CONJ ? -lo.y : lo.y;
+    R re = fma(v.x, lo.x, -v.y * ly);
+    R im = fma(v.x, ly, v.y * lo.x);
+    re = fma(v.x, hi.x, fma(-v.y, hy, re));
+    im = fma(v.x, hy, fma(v.y, hi.x, im));
+    return C{re, im};
+  }
+}
+
+template <typename R> __device__ __forceinline__ R hi_part(double v) { return (R)v; }
+template <typename R> __device__ __forceinline__ R lo_part(double v) {
+  return sizeof(R) == 8 ? (R)0 : (R)(v - (double)(float)v);
+}
+
+// a * W_N^{k} with W_N = exp(-2 pi i / N) (forward) or its conjugate (inverse).
+// k is a compile-time constant after unrolling; trivial factors cost nothing,
+// the others use compensated constants (see cmul_hl).
+template <int N, bool INV, typename C>
+__device__ __forceinline__ C twiddle_const(C a, int k) {
+  using R = typename Re<C>::type;
+  if (k == 0) return a;
+  if (4 * k == N) return INV ? C{-a.y, a.x} : C{a.y, -a.x};          // * (+i) / (-i)
+  constexpr double r2 = 0.70710678118654752440;                       // 1/sqrt(2)
+  if (8 * k == N || 8 * k == 3 * N) {
+    // (+-1 -+ i)/sqrt2: sums first, then one compensated scaling
+    const R rh = hi_part<R>(r2), rl = lo_part<R>(r2);
+    R u, w;
+    if (8 * k == N) {
+      if (INV) { u = a.x - a.y; w = a.x + a.y; } else { u = a.x + a.y; w = a.y - a.x; }
+    } else {
+      if (INV) { u = -a.x - a.y; w = a.x - a.y; } else { u = a.y - a.x; w = -a.x - a.y; }
+    }
+    return C{fma(u, rh, u * rl), fma(w, rh, w * rl)};
+  }
+  const int j = k * (16 / N);
+  const C hi{hi_part<R>(cos16(j)), hi_part<R>(-sin16(j))};
+  const C lo{lo_part<R>(cos16(j)), lo_part<R>(-sin16(j))};
+  return cmul_hl<INV>(a, hi, lo);                                     // * (c - i s) or its conjugate
+}
+
+// In-register DFT of length N in {1,2,4,8,16}: natural order in and out,
+// forward sum e^{-2 pi i jk/N}, inverse e^{+...} without the 1/N.
+template <int N, bool INV, typename C>
+__device__ __forceinline__ void dft_reg(C* v) {
+  if constexpr (N == 1) {
+    return;
+  } else if constexpr (N == 2) {
+    const C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else {
+    static_assert(N == 4 || N == 8 || N == 16, "register DFT length");
+    C e[N / 2], o[N / 2];
+#pragma unroll
+    for (int j = 0; j < N / 2; ++j) {
+      e[j] = v[2 * j];
+      o[j] = v[2 * j + 1];
+    }
+    dft_reg<N / 2, INV>(e);
+    dft_reg<N / 2, INV>(o);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const C t = twiddle_const<N, INV>(o[k], k);
+      v[k] = cadd(e[k], t);
+      v[k + N / 2] = csub(e[k], t);
+    }
+  }
+}
+
+// Split of an axis length into (N1, N2): N <= 16 is one register pass.
+template <int N> struct Split {
+  static constexpr int N1 = (N <= 16) ? N : (N >= 128 ? 16 : 8);
+  static constexpr int N2 = N / N1;
+  static_assert(N1 <= 16 && N2 <= 16 && N1 * N2 == N, "axis length");
+};
+
+}  // namespace hom

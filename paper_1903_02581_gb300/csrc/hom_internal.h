@@ -1,0 +1,37 @@
+// hom_internal.h -- launch interface between the C ABI (hom_api.cu) and the
+// per-precision kernel translation units (hom_kern_c64.cu, hom_kern_c128.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "hom_pass.cuh"
+
+namespace hom {
+
+struct GeoInfo {
+  int G;              // planes per CTA
+  int NT;             // threads per CTA
+  size_t smem;        // dynamic shared memory bytes
+  int tiles_per_sim;  // CTAs per simulation
+};
+
+// Tile geometry of the row (col = false) or column (col = true) pass.
+// G = 0 if (nx, ny) is not a supported size.
+template <typename T> GeoInfo geo_info(int nx, int ny, bool col);
+
+template <typename T>
+cudaError_t launch_kinetic(int nx, int ny, bool col, const PassArgs<typename Cx<T>::type>& a, int batch,
+                           cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_measure(int nx, int ny, bool col, const MeasureArgs<typename Cx<T>::type>& a, int batch,
+                           cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_slater(void* psi, const double2* pk, const double* coef, const int* exch, int b0, int nb,
+                          int n, cudaStream_t s);
+
+cudaError_t launch_reduce(const double* partial, int tiles_per_sim, int batch, double* out, cudaStream_t s);
+
+}  // namespace hom

@@ -1,0 +1,11 @@
+// Kernels of libhom in complex64 (FP32 arithmetic, FP64 reductions).
+#define HOM_T float
+#define HOM_WIDE 1
+#include "hom_kern.inc"
+
+namespace hom {
+cudaError_t launch_reduce(const double* partial, int tiles_per_sim, int batch, double* out, cudaStream_t s) {
+  reduce_partials<NPART><<<batch, 256, 0, s>>>(partial, tiles_per_sim, out);
+  return cudaGetLastError();
+}
+}  // namespace hom

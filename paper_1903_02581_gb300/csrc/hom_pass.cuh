@@ -1,0 +1,550 @@
+// hom_pass.cuh -- the per-particle kinetic passes of one Strang step and the
+// observables passes, templated on precision and grid.
+//
+// The Strang step of Eq. (evoloperat) of arXiv:1903.02581 (symmetric order)
+//   S = V/2 . F_x^-1 T_x/2 F_y^-1 T_y F_y T_x/2 F_x . V/2
+// has a kinetic factor that splits exactly per particle, because every
+// operator of particle 1 commutes with every operator of particle 2 and
+// F_{x1,x2} = F_{x1} F_{x2}, T_x = T_x1 + T_x2 (Appendix A):
+//   K = K_1 K_2,  K_i = F_xi^-1 Q_i F_yi^-1 G_i F_yi Q_i F_xi,
+//   Q_i = e^{-i dt/4 (k_xi - B y_i)^2},  G_i = e^{-i dt/2 k_yi^2}.
+// K_2 acts on the contiguous (x2, y2) plane of each fixed (x1, y1): the
+// "row pass"; K_1 acts on the (x1, y1) plane of each fixed (x2, y2), whose
+// elements are n = nx*ny apart: the "column pass".  The real-space phase
+// e^{-iV tau} (V1(r1) + V1(r2) + V12) is fused into the load of the row pass
+// and, for the last half step, into the store of the column pass.  Each pass
+// reads and writes the state once: two HBM round trips per step.
+//
+// A CTA holds G planes of one simulation in shared memory, laid out
+// [g][x][y] with row stride RS = ny + 1 and plane stride PS (padding chosen so
+// that the access patterns below are free of bank conflicts).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hom_fft.cuh"
+
+namespace hom {
+
+template <typename C> struct PassArgs {
+  C* psi;              // state [batch][n][n]
+  // Unit-modulus phase tables are stored as deltas d = w - 1 (see apply_delta).
+  const C* qa;         // e^{-i dt/4 (k_x - B y)^2} - 1        [x position][y]
+  const C* qt;         // the same table transposed            [y][x position]
+  const C* gy;         // e^{-i dt/2 k_y^2} - 1                [y position]
+  const C* twx;        // e^{-2 pi i j / nx}, j < nx: hi parts, then lo parts
+  const C* twy;        // e^{-2 pi i j / ny}, j < ny: hi parts, then lo parts
+  const C* p1;         // e^{-i tau V1(r)} - 1                 [batch][n]   (tau = dt/2 or dt)
+  const C* p12;        // e^{-i tau V12(dx, dy)} - 1           [batch][(2nx-1)(2ny-1)]
+  int apply_v;         // row pass: phase at load; column pass: phase at store
+  int pref_ahead;      // row pass: prefetch into L2 the tile this many CTAs ahead (0: off)
+};
+
+template <typename C> struct MeasureArgs {
+  const C* psi;
+  const C* twx;
+  const C* twy;
+  const double* tx;    // 1/2 (k_x - B y)^2                    [x position][y]
+  const double* ty;    // 1/2 k_y^2                            [y position]
+  const double* v1;    // V1(r)                                [batch][n]
+  const double* v12;   // V12(dx, dy)                          [batch][(2nx-1)(2ny-1)]
+  double* partial;     // [tile][NPART]
+};
+
+constexpr int NPART = 6;   // norm, e_pot, e_coul, p_bunch, e_tx, e_ty (raw sums)
+
+template <typename T, int NX, int NY, bool COL> struct Geo {
+  using C = typename Cx<T>::type;
+  static constexpr int N = NX * NY;
+  static constexpr int LW = 128 / (int)sizeof(C);        // lanes per shared-memory wavefront
+  static constexpr int BUDGET = (COL ? 16384 : 4096) * 8 / (int)sizeof(C);
+  static constexpr int GMAX = COL ? 16 : 8;
+  static constexpr int G0 = BUDGET / N;
+  static constexpr int G = G0 < 1 ? 1 : (G0 > GMAX ? GMAX : G0);
+  static constexpr int RS = NY + 1;
+  static constexpr int PS0 = NX * RS;
+  static constexpr int PSM = (G >= LW) ? 1 : (LW / G);
+  static constexpr int PS = PS0 + ((((PSM - PS0) % LW) + LW) % LW);
+  static constexpr int ELEMS = G * PS;
+  static constexpr int NT = (G * N >= 8192) ? 512 : 256;
+  static constexpr size_t SMEM = (size_t)(ELEMS + 2 * NX + 2 * NY) * sizeof(C);
+  static constexpr int TILES_PER_SIM = N / G;
+  static_assert(N % G == 0, "tile");
+  // Column pass with fewer than 4 planes per CTA: a cluster of CL CTAs owns
+  // CL*G adjacent columns, so that its loads and stores cover whole 32-byte
+  // sectors of each row; planes move between the CTAs through distributed
+  // shared memory.
+  static constexpr int CL = (COL && G < 4) ? 4 / G : 1;
+  static_assert(TILES_PER_SIM % CL == 0, "cluster");
+};
+
+// ---------------------------------------------------------------------------
+// Line transforms over the shared-memory planes.  An x-line is the column of
+// one (g, y); a y-line is the row of one (g, x position).
+// ---------------------------------------------------------------------------
+
+struct NoHook {
+  template <typename C> __device__ __forceinline__ C operator()(int, int, C v) const { return v; }
+};
+
+// Forward DFT along x of every x-line; hook(pos, y, v) sees each output
+// coefficient at its x position (digit-transposed order when nx > 16).
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, class Hook>
+__device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  const int tid = threadIdx.x;
+  if constexpr (N2 == 1) {
+    for (int it = tid; it < G * NY; it += NT) {
+      const int y = it % NY, g = it / NY;
+      C* line = sm + g * PS + y;
+      C v[NX];
+#pragma unroll
+      for (int x = 0; x < NX; ++x) v[x] = line[x * RS];
+      dft_reg<NX, false>(v);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
+    }
+    __syncthreads();
+  } else {
+    for (int it = tid; it < G * NY * N2; it += NT) {
+      const int y = it % NY, n2 = (it / NY) % N2, g = it / (NY * N2);
+      C* line = sm + g * PS + y;
+      C v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = line[(N2 * n1 + n2) * RS];
+      dft_reg<N1, false>(v);
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NX + n2 * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + n2) * RS] = v[k1];
+    }
+    __syncthreads();
+    for (int it = tid; it < G * NY * N1; it += NT) {
+      const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
+      C* line = sm + g * PS + y;
+      C v[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = line[(N2 * k1 + n2) * RS];
+      dft_reg<N2, false>(v);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) line[(N2 * k1 + k2) * RS] = hook(N2 * k1 + k2, y, v[k2]);
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse DFT along x (no 1/nx), digit-transposed positions in, natural out.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS>
+__device__ __forceinline__ void x_inverse(C* sm, const C* tw) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  const int tid = threadIdx.x;
+  if constexpr (N2 == 1) {
+    for (int it = tid; it < G * NY; it += NT) {
+      const int y = it % NY, g = it / NY;
+      C* line = sm + g * PS + y;
+      C v[NX];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v[k] = line[k * RS];
+      dft_reg<NX, true>(v);
+#pragma unroll
+      for (int x = 0; x < NX; ++x) line[x * RS] = v[x];
+    }
+    __syncthreads();
+  } else {
+    for (int it = tid; it < G * NY * N1; it += NT) {
+      const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
+      C* line = sm + g * PS + y;
+      C v[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[(N2 * k1 + k2) * RS];
+      dft_reg<N2, true>(v);
+#pragma unroll
+      for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_hl<true>(v[m1], tw[m1 * k1], tw[NX + m1 * k1]);
+#pragma unroll
+      for (int m1 = 0; m1 < N2; ++m1) line[(N2 * k1 + m1) * RS] = v[m1];
+    }
+    __syncthreads();
+    for (int it = tid; it < G * NY * N2; it += NT) {
+      const int y = it % NY, m1 = (it / NY) % N2, g = it / (NY * N2);
+      C* line = sm + g * PS + y;
+      C v[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[(N2 * k1 + m1) * RS];
+      dft_reg<N1, true>(v);
+#pragma unroll
+      for (int m2 = 0; m2 < N1; ++m2) line[(m1 + N2 * m2) * RS] = v[m2];
+    }
+    __syncthreads();
+  }
+}
+
+// The y part of the kinetic sandwich on every y-line: F_y, G, F_y^-1 (no
+// 1/ny), then the second T_x/2 phase qb (a [y][x position] table, so that
+// lanes running over x positions read consecutive entries) and the 1/(nx ny)
+// of both inverse transforms (a power of two: exact).
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS>
+__device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restrict__ gy,
+                                           const C* __restrict__ qb) {
+  using S = Split<NY>;
+  using R = typename Re<C>::type;
+  constexpr R scale = (R)1 / (R)(NX * NY);
+  constexpr int N1 = S::N1, N2 = S::N2;
+  const int tid = threadIdx.x;
+  if constexpr (N2 == 1) {
+    for (int it = tid; it < G * NX; it += NT) {
+      const int px = it % NX, g = it / NX;
+      C* row = sm + g * PS + px * RS;
+      C v[NY];
+#pragma unroll
+      for (int y = 0; y < NY; ++y) v[y] = row[y];
+      dft_reg<NY, false>(v);
+#pragma unroll
+      for (int k = 0; k < NY; ++k) v[k] = apply_delta(v[k], ldg(gy + k));
+      dft_reg<NY, true>(v);
+#pragma unroll
+      for (int y = 0; y < NY; ++y) row[y] = apply_delta(C{v[y].x * scale, v[y].y * scale}, ldg(qb + y * NX + px));
+    }
+    __syncthreads();
+  } else {
+    for (int it = tid; it < G * NX * N2; it += NT) {
+      const int px = it % NX, n2 = (it / NX) % N2, g = it / (NX * N2);
+      C* row = sm + g * PS + px * RS;
+      C v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = row[N2 * n1 + n2];
+      dft_reg<N1, false>(v);
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NY + n2 * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1 + n2] = v[k1];
+    }
+    __syncthreads();
+    for (int it = tid; it < G * NX * N1; it += NT) {
+      const int px = it % NX, k1 = (it / NX) % N1, g = it / (NX * N1);
+      C* row = sm + g * PS + px * RS;
+      C v[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = row[N2 * k1 + n2];
+      dft_reg<N2, false>(v);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) v[k2] = apply_delta(v[k2], ldg(gy + N2 * k1 + k2));
+      dft_reg<N2, true>(v);
+#pragma unroll
+      for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_hl<true>(v[m1], tw[m1 * k1], tw[NY + m1 * k1]);
+#pragma unroll
+      for (int m1 = 0; m1 < N2; ++m1) row[N2 * k1 + m1] = v[m1];
+    }
+    __syncthreads();
+    for (int it = tid; it < G * NX * N2; it += NT) {
+      const int px = it % NX, m1 = (it / NX) % N2, g = it / (NX * N2);
+      C* row = sm + g * PS + px * RS;
+      C v[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) v[k1] = row[N2 * k1 + m1];
+      dft_reg<N1, true>(v);
+#pragma unroll
+      for (int m2 = 0; m2 < N1; ++m2) {
+        const int y = m1 + N2 * m2;
+        row[y] = apply_delta(C{v[m2].x * scale, v[m2].y * scale}, ldg(qb + y * NX + px));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Forward DFT along y of every y-line; hook(pos_x, pos_y, v) sees each output.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, class Hook>
+__device__ __forceinline__ void y_forward(C* sm, const C* tw, Hook& hook) {
+  using S = Split<NY>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  const int tid = threadIdx.x;
+  if constexpr (N2 == 1) {
+    for (int it = tid; it < G * NX; it += NT) {
+      const int px = it % NX, g = it / NX;
+      C* row = sm + g * PS + px * RS;
+      C v[NY];
+#pragma unroll
+      for (int y = 0; y < NY; ++y) v[y] = row[y];
+      dft_reg<NY, false>(v);
+#pragma unroll
+      for (int k = 0; k < NY; ++k) row[k] = hook(px, k, v[k]);
+    }
+    __syncthreads();
+  } else {
+    for (int it = tid; it < G * NX * N2; it += NT) {
+      const int px = it % NX, n2 = (it / NX) % N2, g = it / (NX * N2);
+      C* row = sm + g * PS + px * RS;
+      C v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = row[N2 * n1 + n2];
+      dft_reg<N1, false>(v);
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NY + n2 * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1 + n2] = v[k1];
+    }
+    __syncthreads();
+    for (int it = tid; it < G * NX * N1; it += NT) {
+      const int px = it % NX, k1 = (it / NX) % N1, g = it / (NX * N1);
+      C* row = sm + g * PS + px * RS;
+      C v[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) v[n2] = row[N2 * k1 + n2];
+      dft_reg<N2, false>(v);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) row[N2 * k1 + k2] = hook(px, N2 * k1 + k2, v[k2]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Real-space phase e^{-i tau V(r1, r2)} from the single-particle and the
+// difference tables (never a 4D array).
+// ---------------------------------------------------------------------------
+template <typename C, int NX, int NY>
+__device__ __forceinline__ C vphase_delta(const C* __restrict__ p1, const C* __restrict__ p12, int r1, int r2) {
+  const int x1 = r1 / NY, y1 = r1 % NY, x2 = r2 / NY, y2 = r2 % NY;
+  const int d = (x1 - x2 + NX - 1) * (2 * NY - 1) + (y1 - y2 + NY - 1);
+  // (1 + d1)(1 + d2)(1 + d12) - 1, formed from the small deltas
+  const C d1 = ldg(p1 + r1), d2 = ldg(p1 + r2), d12 = ldg(p12 + d);
+  const C e = cadd(cadd(d1, d2), cmul(d1, d2));
+  return cadd(cadd(e, d12), cmul(e, d12));
+}
+
+template <typename C, int NY>
+struct QHook {
+  const C* __restrict__ q;
+  __device__ __forceinline__ C operator()(int pos, int y, C v) const { return apply_delta(v, ldg(q + pos * NY + y)); }
+};
+
+// ---------------------------------------------------------------------------
+// Kinetic pass: row (COL = false, particle 2) or column (COL = true, particle 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <typename T, int NX, int NY, bool COL>
+__global__ void __launch_bounds__(Geo<T, NX, NY, COL>::NT)
+kinetic_pass(PassArgs<typename Cx<T>::type> a) {
+  using Gm = Geo<T, NX, NY, COL>;
+  using C = typename Cx<T>::type;
+  constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS, CL = Gm::CL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  C* stwx = sm + Gm::ELEMS;
+  C* stwy = stwx + 2 * NX;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
+  for (int i = tid; i < 2 * NY; i += NT) stwy[i] = a.twy[i];
+
+  const int tile = blockIdx.x;
+  const int b = tile / Gm::TILES_PER_SIM;
+  const int t0 = (tile % Gm::TILES_PER_SIM) * G;
+  C* base = a.psi + (size_t)b * N * N;
+  const C* p1 = a.p1 + (size_t)b * N;
+  const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
+
+  if constexpr (!COL) {
+    // rows: G contiguous planes; start the HBM read of a later tile into L2
+    if (tid == 0 && a.pref_ahead > 0 && tile + a.pref_ahead < (int)gridDim.x) {
+      const int nt = tile + a.pref_ahead;
+      const C* p = a.psi + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
+      prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
+    }
+    for (int e = tid; e < G * N; e += NT) {
+      const int g = e / N, r = e % N;
+      C v = base[(size_t)(t0 + g) * N + r];
+      if (a.apply_v) v = apply_delta(v, vphase_delta<C, NX, NY>(p1, p12, t0 + g, r));
+      sm[g * PS + (r / NY) * RS + (r % NY)] = v;
+    }
+    __syncthreads();
+  } else if constexpr (CL == 1) {
+    for (int e = tid; e < G * N; e += NT) {
+      const int g = e % G, r = e / G;
+      sm[g * PS + (r / NY) * RS + (r % NY)] = base[(size_t)r * N + (t0 + g)];
+    }
+    __syncthreads();
+  } else {
+    // cluster: this CTA loads rows [q N/CL, (q+1) N/CL) of the cluster's CL*G
+    // columns and deals each element to the CTA owning its column
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank();
+    const int c0 = t0 - q * G;
+    constexpr int W = CL * G, ROWS = N / CL;
+    cl.sync();                                   // every CTA of the cluster is running
+    for (int e = tid; e < ROWS * W; e += NT) {
+      const int j = e % W, r = q * ROWS + e / W;
+      const C v = base[(size_t)r * N + c0 + j];
+      C* dst = cl.map_shared_rank(sm, j / G);
+      dst[(j % G) * PS + (r / NY) * RS + (r % NY)] = v;
+    }
+    cl.sync();
+  }
+
+  QHook<C, NY> qa{a.qa};
+  x_forward<C, NX, NY, G, NT, RS, PS>(sm, stwx, qa);
+  y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
+  x_inverse<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+
+  if constexpr (!COL) {
+    for (int e = tid; e < G * N; e += NT) {
+      const int g = e / N, r = e % N;
+      base[(size_t)(t0 + g) * N + r] = sm[g * PS + (r / NY) * RS + (r % NY)];
+    }
+  } else if constexpr (CL == 1) {
+    for (int e = tid; e < G * N; e += NT) {
+      const int g = e % G, r = e / G;
+      C v = sm[g * PS + (r / NY) * RS + (r % NY)];
+      if (a.apply_v) v = apply_delta(v, vphase_delta<C, NX, NY>(p1, p12, r, t0 + g));
+      base[(size_t)r * N + (t0 + g)] = v;
+    }
+  } else {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank();
+    const int c0 = t0 - q * G;
+    constexpr int W = CL * G, ROWS = N / CL;
+    cl.sync();                                   // every CTA has finished its planes
+    for (int e = tid; e < ROWS * W; e += NT) {
+      const int j = e % W, r = q * ROWS + e / W;
+      const C* src = cl.map_shared_rank(sm, j / G);
+      C v = src[(j % G) * PS + (r / NY) * RS + (r % NY)];
+      if (a.apply_v) v = apply_delta(v, vphase_delta<C, NX, NY>(p1, p12, r, c0 + j));
+      base[(size_t)r * N + c0 + j] = v;
+    }
+    cl.sync();                                   // keep this CTA's planes alive for the readers
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Observables: raw sums per tile, FP64 accumulation.
+// ---------------------------------------------------------------------------
+template <typename C, int NY>
+struct AccHook {
+  const double* __restrict__ w;   // weight by (pos, other)
+  double acc;
+  bool by_first;                  // x hook: w[pos * NY + y]; y hook: w[y position]
+  __device__ __forceinline__ C operator()(int p, int q, C v) {
+    const double wt = by_first ? w[p * NY + q] : w[q];
+    acc += wt * (double)cnorm2(v);
+    return v;
+  }
+};
+
+template <typename T> __device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  }
+  return s;   // valid in thread 0
+}
+
+template <typename T, int NX, int NY, bool COL>
+__global__ void __launch_bounds__(Geo<T, NX, NY, COL>::NT)
+measure_pass(MeasureArgs<typename Cx<T>::type> a) {
+  using Gm = Geo<T, NX, NY, COL>;
+  using C = typename Cx<T>::type;
+  constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  C* stwx = sm + Gm::ELEMS;
+  C* stwy = stwx + 2 * NX;
+  __shared__ double red[32];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
+  for (int i = tid; i < 2 * NY; i += NT) stwy[i] = a.twy[i];
+
+  const int tile = blockIdx.x;
+  const int b = tile / Gm::TILES_PER_SIM;
+  const int t0 = (tile % Gm::TILES_PER_SIM) * G;
+  const C* base = a.psi + (size_t)b * N * N;
+  const double* v1 = a.v1 + (size_t)b * N;
+  const double* v12 = a.v12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
+
+  double s_norm = 0.0, s_pot = 0.0, s_coul = 0.0, s_pb = 0.0;
+  for (int e = tid; e < G * N; e += NT) {
+    int g, r;
+    size_t off;
+    if constexpr (!COL) { g = e / N; r = e % N; off = (size_t)(t0 + g) * N + r; }
+    else                { g = e % G; r = e / G; off = (size_t)r * N + (t0 + g); }
+    const C v = base[off];
+    if constexpr (!COL) {
+      const int r1 = t0 + g, r2 = r;
+      const double rho = (double)cnorm2(v);
+      const int x1 = r1 / NY, y1 = r1 % NY, x2 = r2 / NY, y2 = r2 % NY;
+      s_norm += rho;
+      s_pot += rho * (v1[r1] + v1[r2]);
+      s_coul += rho * v12[(x1 - x2 + NX - 1) * (2 * NY - 1) + (y1 - y2 + NY - 1)];
+      if ((x1 < NX / 2) == (x2 < NX / 2)) s_pb += rho;
+    }
+    sm[g * PS + (r / NY) * RS + (r % NY)] = v;
+  }
+  __syncthreads();
+
+  AccHook<C, NY> hx{a.tx, 0.0, true};
+  x_forward<C, NX, NY, G, NT, RS, PS>(sm, stwx, hx);
+  AccHook<C, NY> hy{a.ty, 0.0, false};
+  y_forward<C, NX, NY, G, NT, RS, PS>(sm, stwy, hy);
+
+  const double vals[NPART] = {s_norm, s_pot, s_coul, s_pb, hx.acc, hy.acc};
+  double* out = a.partial + (size_t)tile * NPART;
+#pragma unroll
+  for (int i = 0; i < NPART; ++i) {
+    const double s = block_sum<T>(vals[i], red);
+    if (tid == 0) out[i] = s;
+  }
+}
+
+// Sum the per-tile partials of each simulation in a fixed order:
+// out[b][i] = sum over tiles of partial[tile][i].
+template <int NP>
+__global__ void reduce_partials(const double* __restrict__ partial, int tiles_per_sim,
+                                double* __restrict__ out) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  for (int i = 0; i < NP; ++i) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < tiles_per_sim; t += blockDim.x)
+      s += partial[((size_t)b * tiles_per_sim + t) * NP + i];
+    s = block_sum<double>(s, red);
+    if (threadIdx.x == 0) out[b * NP + i] = s;
+  }
+}
+
+// psi[b][r1][r2] = c_b (alpha[r1] beta[r2] + s_b beta[r1] alpha[r2]) in FP64,
+// rounded once to the state precision (Eq. twopstate).
+template <typename C>
+__global__ void slater_init(C* __restrict__ psi, const double2* __restrict__ pk, const double* __restrict__ coef,
+                            const int* __restrict__ exch, int b0, int nb, int n) {
+  const size_t per = (size_t)n * n;
+  const size_t total = per * nb;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = b0 + (int)(i / per);
+    const size_t j = i % per;
+    const int r1 = (int)(j / n), r2 = (int)(j % n);
+    const double2* al = pk + (size_t)b * 2 * n;
+    const double2* be = al + n;
+    const double2 a1 = al[r1], b2 = be[r2], b1 = be[r1], a2 = al[r2];
+    double re = a1.x * b2.x - a1.y * b2.y, im = a1.x * b2.y + a1.y * b2.x;
+    const double s = (double)exch[b];
+    re += s * (b1.x * a2.x - b1.y * a2.y);
+    im += s * (b1.x * a2.y + b1.y * a2.x);
+    const double c = coef[b];
+    using R = typename Re<C>::type;
+    psi[(size_t)b * per + j] = C{(R)(c * re), (R)(c * im)};
+  }
+}
+
+}  // namespace hom
