@@ -57,8 +57,8 @@ typedef enum { HOM_C64 = 0, HOM_C128 = 1 } hom_prec;
  * {16,32,64}; HOM_C128 needs nx*ny <= 8192.  dt may be negative (backward
  * propagation).  qpc_h, qpc_w and coul_lambda are defaults for every
  * simulation of the batch (see hom_set_sim_params).  ckpt_slots reserves
- * room in the workspace for that many state checkpoints of hom_backward
- * (0 if hom_backward is not used). */
+ * room in the workspace for that many state checkpoints of hom_backward plus
+ * one adjoint state (0 if hom_backward is not used). */
 typedef struct {
   int32_t nx, ny, batch, prec;
   double dx, dy, B, omega_y, dt;
@@ -129,14 +129,19 @@ hom_status hom_step(hom_ctx* ctx, int32_t nsteps);
  * not finite. */
 hom_status hom_observables(hom_ctx* ctx, hom_obs* out);
 
-/* Adjoint gradient of L_b = p_bunch of simulation b after nsteps steps.
- * Starts from the current state, which must have been set by
- * hom_init_packets (the packets define d psi0 / d delay, delay being the
- * centre of beta); keeps checkpoints every K steps in the workspace
- * (ceil(nsteps/K) <= ckpt_slots), recomputes each segment forward and runs
- * the adjoint step S(dt)^dagger = S(-dt) backward.  loss[b] = L_b,
- * grad[3*b + {0,1,2}] = dL_b / d{qpc_h, qpc_w, delay} (host arrays).  Leaves
- * the state at step nsteps.  Synchronises the stream. */
+/* Adjoint gradient of L_b = p_bunch of simulation b after nsteps steps
+ * (Eq. p_bunching).  Starts from the current state, which must have been set
+ * by hom_init_packets (the packets define d psi0 / d delay, delay being the
+ * centre of beta).  Runs forward keeping a checkpoint every K steps in the
+ * workspace (ceil(nsteps/K) <= ckpt_slots), then backward: the adjoint state
+ * lambda_N = M psi_N is stepped with S(dt)^dagger = S(-dt) (the Strang
+ * product is palindromic and unitary), psi_n is restored from a checkpoint
+ * or by S(-dt) psi_{n+1}, and dL/dtheta = 2 dt dV Im sum'_n <lambda_n|
+ * dV/dtheta |psi_n> (trapezoid weights), dL/ddelay = 2 dV Re <lambda_0|
+ * d psi_0/d delay>.  loss[b] = L_b, grad[3*b + {0,1,2}] = dL_b /
+ * d{qpc_h, qpc_w, delay} (host arrays).  Leaves the state at step 0 (the
+ * initial state).  Synchronises the stream.  HOM_ERR_ARG if ckpt_slots is too
+ * small, HOM_ERR_STATE if a simulation was not initialised from packets. */
 hom_status hom_backward(hom_ctx* ctx, int32_t nsteps, int32_t K, double* loss,
                         double* grad);
 

@@ -11,6 +11,7 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -67,7 +68,8 @@ struct Layout {
   size_t tx, ty, v1, v12;
   size_t part_row, part_col, obs;
   size_t packets, dbeta, coef, exch, scratch;
-  size_t ckpt;
+  size_t adj_slot1, adj_slot2, adj_dv, adj_cdc, adj_out;
+  size_t lam, ckpt;
   size_t total;
   int tiles_row, tiles_col;
 };
@@ -153,6 +155,12 @@ Layout make_layout(const hom_params& p) {
   L.coef = take(B * 8);
   L.exch = take(B * 4);
   L.scratch = take(B * 8 * 8);
+  L.adj_slot1 = take(B * hom::kAdjBlocks * 8);
+  L.adj_slot2 = take(B * hom::kAdjBlocks * 2 * 8);
+  L.adj_dv = take(B * 2 * p.nx * 8);
+  L.adj_cdc = take(B * 2 * 8);
+  L.adj_out = take(B * 4 * 8);
+  L.lam = take(p.ckpt_slots > 0 ? B * n * n * eb : 0);
   L.ckpt = take((size_t)p.ckpt_slots * B * n * n * eb);
   L.total = o;
   return L;
@@ -426,11 +434,11 @@ hom_status prof_end(hom_ctx* c, size_t idx, int kind) {
 }
 
 template <typename T>
-hom_status step_sequence(hom_ctx* c, int nsteps, int sgn) {
+hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   using C = typename hom::Cx<T>::type;
   const hom_params& p = c->p;
   hom::PassArgs<C> a{};
-  a.psi = reinterpret_cast<C*>(c->state);
+  a.psi = reinterpret_cast<C*>(psi);
   a.qa = reinterpret_cast<const C*>(c->ws + c->L.qa[sgn]);
   a.qt = reinterpret_cast<const C*>(c->ws + c->L.qt[sgn]);
   a.gy = reinterpret_cast<const C*>(c->ws + c->L.gy[sgn]);
@@ -459,8 +467,9 @@ hom_status step_sequence(hom_ctx* c, int nsteps, int sgn) {
   return HOM_OK;
 }
 
-hom_status run_steps(hom_ctx* c, int nsteps, int sgn) {
-  return c->p.prec == HOM_C128 ? step_sequence<double>(c, nsteps, sgn) : step_sequence<float>(c, nsteps, sgn);
+hom_status run_steps(hom_ctx* c, char* psi, int nsteps, int sgn) {
+  return c->p.prec == HOM_C128 ? step_sequence<double>(c, psi, nsteps, sgn)
+                               : step_sequence<float>(c, psi, nsteps, sgn);
 }
 
 template <typename T>
@@ -581,6 +590,16 @@ hom_status hom_init_packets(hom_ctx* c, int32_t b, const hom_packet* alpha, cons
   if (!(sum > 1e-12 * na * nb) || !(sum * dV > 1e-300))
     return fail(c, HOM_ERR_ARG, "the combined state vanishes (identical packets?)");
   const double coef = 1.0 / std::sqrt(sum * dV);
+  // d(sum)/d(beta centre) for d psi0 / d delay:
+  // 2 Re[ na <b|db> (1 + s^2) + 2 s <b|a> <a|db> ]
+  cd bdb(0, 0), adb(0, 0);
+  for (size_t i = 0; i < n; ++i) {
+    bdb += std::conj(be[i]) * dbe[i];
+    adb += std::conj(a[i]) * dbe[i];
+  }
+  const double sx = (double)exch;
+  const double dsum = 2.0 * (na * bdb * (1.0 + sx * sx) + 2.0 * sx * std::conj(ab) * adb).real();
+  const double cdc[2] = {coef, -0.5 * coef * dsum / sum};
   const int b0 = b < 0 ? 0 : b, b1 = b < 0 ? p.batch : b + 1;
   std::vector<double2> host(2 * n), dhost(n);
   for (size_t i = 0; i < n; ++i) {
@@ -593,6 +612,7 @@ hom_status hom_init_packets(hom_ctx* c, int32_t b, const hom_packet* alpha, cons
     if ((s = upload(c, c->L.dbeta + (size_t)bb * n * 16, dhost.data(), n * 16)) != HOM_OK) return s;
     if ((s = upload(c, c->L.coef + (size_t)bb * 8, &coef, 8)) != HOM_OK) return s;
     if ((s = upload(c, c->L.exch + (size_t)bb * 4, &exch, 4)) != HOM_OK) return s;
+    if ((s = upload(c, c->L.adj_cdc + (size_t)bb * 16, cdc, 16)) != HOM_OK) return s;
     c->have_packets[bb] = 1;
     c->exch[bb] = exch;
   }
@@ -611,7 +631,7 @@ hom_status hom_step(hom_ctx* c, int32_t nsteps) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if (nsteps < 0) return fail(c, HOM_ERR_ARG, "nsteps must be >= 0");
-  return run_steps(c, nsteps, 0);
+  return run_steps(c, c->state, nsteps, 0);
 }
 
 hom_status hom_observables(hom_ctx* c, hom_obs* out) {
@@ -645,11 +665,87 @@ hom_status hom_observables(hom_ctx* c, hom_obs* out) {
 hom_status hom_backward(hom_ctx* c, int32_t nsteps, int32_t K, double* loss, double* grad) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
-  (void)nsteps;
-  (void)K;
-  (void)loss;
-  (void)grad;
-  return fail(c, HOM_ERR_STATE, "hom_backward is not available in this build");
+  const hom_params& p = c->p;
+  if (!loss || !grad) return fail(c, HOM_ERR_ARG, "loss and grad must be non-NULL");
+  if (nsteps < 1 || K < 1) return fail(c, HOM_ERR_ARG, "nsteps and K must be >= 1");
+  const int S = (nsteps + K - 1) / K;
+  if (S > p.ckpt_slots)
+    return fail(c, HOM_ERR_ARG, "%d checkpoints needed (nsteps=%d, K=%d) but ckpt_slots=%d", S, nsteps, K,
+                p.ckpt_slots);
+  for (int b = 0; b < p.batch; ++b)
+    if (!c->have_packets[b])
+      return fail(c, HOM_ERR_STATE, "simulation %d was not set by hom_init_packets (needed for d/d delay)", b);
+  const bool dbl = p.prec == HOM_C128;
+  const int nx = p.nx, ny = p.ny, n = nx * ny;
+  const size_t total = (size_t)p.batch * n * n * elem_bytes(p);
+  // dV1/dh and dV1/dw along x for every simulation
+  std::vector<double> dv((size_t)p.batch * 2 * nx);
+  for (int b = 0; b < p.batch; ++b) {
+    const SimParams& sp = c->sims[b];
+    for (int ix = 0; ix < nx; ++ix) {
+      const double x = coord(nx, p.dx, ix) - p.qpc_x0;
+      const double g = std::exp(-x * x / (2.0 * sp.w * sp.w));
+      dv[(size_t)b * 2 * nx + ix] = g;
+      dv[(size_t)b * 2 * nx + nx + ix] = sp.h * g * x * x / (sp.w * sp.w * sp.w);
+    }
+  }
+  if ((s = upload(c, c->L.adj_dv, dv.data(), dv.size() * 8)) != HOM_OK) return s;
+  char* ckpt = c->ws + c->L.ckpt;
+  char* lam = c->ws + c->L.lam;
+  double* slot1 = reinterpret_cast<double*>(c->ws + c->L.adj_slot1);
+  double* slot2 = reinterpret_cast<double*>(c->ws + c->L.adj_slot2);
+  double* out = reinterpret_cast<double*>(c->ws + c->L.adj_out);
+  const double* dvd = reinterpret_cast<const double*>(c->ws + c->L.adj_dv);
+  // forward, keeping psi_{jK}
+  for (int j = 0; j < S; ++j) {
+    HOM_CUDA(c, cudaMemcpyAsync(ckpt + (size_t)j * total, c->state, total, cudaMemcpyDeviceToDevice, c->stream));
+    const int m = std::min(K, nsteps - j * K);
+    if ((s = run_steps(c, c->state, m, 0)) != HOM_OK) return s;
+  }
+  // loss and lambda_N = M psi_N
+  if (dbl) HOM_CUDA(c, hom::launch_adj_mask<double>(c->state, lam, slot1, nx, ny, p.batch, c->stream));
+  else HOM_CUDA(c, hom::launch_adj_mask<float>(c->state, lam, slot1, nx, ny, p.batch, c->stream));
+  HOM_CUDA(c, hom::launch_adj_reduce(slot1, 1, p.batch, out, 4, c->stream));
+  HOM_CUDA(c, cudaMemsetAsync(slot2, 0, (size_t)p.batch * hom::kAdjBlocks * 2 * 8, c->stream));
+  auto accum = [&](double w) -> hom_status {
+    if (dbl) HOM_CUDA(c, hom::launch_adj_accum<double>(c->state, lam, dvd, slot2, w, nx, ny, p.batch, c->stream));
+    else HOM_CUDA(c, hom::launch_adj_accum<float>(c->state, lam, dvd, slot2, w, nx, ny, p.batch, c->stream));
+    return HOM_OK;
+  };
+  if ((s = accum(0.5)) != HOM_OK) return s;
+  // backward: psi_n from the checkpoint or by S(-dt) psi_{n+1}; lambda_n = S(-dt) lambda_{n+1}
+  for (int m = nsteps - 1; m >= 0; --m) {
+    if (m % K == 0) {
+      HOM_CUDA(c, cudaMemcpyAsync(c->state, ckpt + (size_t)(m / K) * total, total, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    } else if ((s = run_steps(c, c->state, 1, 1)) != HOM_OK) {
+      return s;
+    }
+    if ((s = run_steps(c, lam, 1, 1)) != HOM_OK) return s;
+    if ((s = accum(m == 0 ? 0.5 : 1.0)) != HOM_OK) return s;
+  }
+  HOM_CUDA(c, hom::launch_adj_reduce(slot2, 2, p.batch, out + 1, 4, c->stream));
+  const double2* pk = reinterpret_cast<const double2*>(c->ws + c->L.packets);
+  const double2* db = reinterpret_cast<const double2*>(c->ws + c->L.dbeta);
+  const double* cdc = reinterpret_cast<const double*>(c->ws + c->L.adj_cdc);
+  const int* ex = reinterpret_cast<const int*>(c->ws + c->L.exch);
+  if (dbl) HOM_CUDA(c, hom::launch_adj_delay<double>(lam, pk, db, cdc, ex, slot1, n, p.batch, c->stream));
+  else HOM_CUDA(c, hom::launch_adj_delay<float>(lam, pk, db, cdc, ex, slot1, n, p.batch, c->stream));
+  HOM_CUDA(c, hom::launch_adj_reduce(slot1, 1, p.batch, out + 3, 4, c->stream));
+  std::vector<double> h((size_t)p.batch * 4);
+  HOM_CUDA(c, cudaMemcpyAsync(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double dV = p.dx * p.dx * p.dy * p.dy;
+  for (int b = 0; b < p.batch; ++b) {
+    loss[b] = dV * h[(size_t)b * 4];
+    grad[3 * b + 0] = 2.0 * p.dt * dV * h[(size_t)b * 4 + 1];
+    grad[3 * b + 1] = 2.0 * p.dt * dV * h[(size_t)b * 4 + 2];
+    grad[3 * b + 2] = 2.0 * dV * h[(size_t)b * 4 + 3];
+    if (!std::isfinite(loss[b]) || !std::isfinite(grad[3 * b]) || !std::isfinite(grad[3 * b + 1]) ||
+        !std::isfinite(grad[3 * b + 2]))
+      return fail(c, HOM_ERR_NUMERIC, "non-finite gradient in simulation %d", b);
+  }
+  return HOM_OK;
 }
 
 hom_status hom_copy_state(hom_ctx* c, int32_t b, void* host, size_t bytes, int32_t to_device) {

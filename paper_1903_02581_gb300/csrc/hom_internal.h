@@ -34,4 +34,17 @@ cudaError_t launch_slater(void* psi, const double2* pk, const double* coef, cons
 
 cudaError_t launch_reduce(const double* partial, int tiles_per_sim, int batch, double* out, cudaStream_t s);
 
+// Adjoint gradient kernels (hom_adjoint.cuh); slots hold kAdjBlocks partial
+// sums per simulation (times 2 for adj_accum).
+constexpr int kAdjBlocks = 512;
+template <typename T>
+cudaError_t launch_adj_mask(const void* psi, void* lam, double* slot, int nx, int ny, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_accum(const void* psi, const void* lam, const double* dv, double* slot, double w, int nx,
+                             int ny, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_delay(const void* lam, const double2* pk, const double2* dbeta, const double* cdc,
+                             const int* exch, double* slot, int n, int batch, cudaStream_t s);
+cudaError_t launch_adj_reduce(const double* slot, int nk, int batch, double* out, int stride, cudaStream_t s);
+
 }  // namespace hom
