@@ -161,6 +161,31 @@ hom_status hom_profile(hom_ctx* ctx, int32_t enable);
 hom_status hom_profile_read(hom_ctx* ctx, double* ms_row, double* ms_col, int64_t* n_row,
                             int64_t* n_col);
 
+/* Norm and bunching probability of a batch of states, for callers that
+ * cannot allocate device memory: code that was handed the state in a buffer
+ * it does not own (another framework's tensor, a slice of a pool) and runs
+ * where cudaMalloc is forbidden or would fail or synchronise.  The paper has
+ * no counterpart; it is the real-space part of hom_observables without a
+ * context or workspace.
+ *   d_state: device, batch states laid out as for hom_create (complex64 if
+ *            prec == HOM_C64, complex128 if HOM_C128), not modified;
+ *   d_out:   device, 2*batch doubles written: d_out[2b] = sum |psi|^2 dx^2 dy^2,
+ *            d_out[2b+1] = probability that x1 and x2 have the same sign;
+ *   nx in {16..256}, ny in {16, 32, 64} (powers of two), dx, dy > 0,
+ *   1 <= batch <= 64 (HOM_ERR_ARG otherwise, nothing launched).
+ * Its partial sums live in one fixed 256 KiB array in the library's device
+ * memory (every GPU that loads the library holds it until the process exits);
+ * nothing is allocated, by the library or by the caller.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current: make that first call before any stream capture.  Every
+ * call writes every partial it later reads, so no clearing is needed, but all
+ * calls share the array: calls whose kernels overlap on the GPU (different
+ * streams, or several host threads) race and must be serialised by the
+ * caller.  Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream).  HOM_ERR_CUDA if a launch or the address lookup fails. */
+hom_status hom_bunching_static(const void* d_state, int32_t prec, int32_t nx, int32_t ny, int32_t batch,
+                               double dx, double dy, double* d_out, void* cuda_stream);
+
 /* Message of the last failure on ctx (or of the last failed hom_create when
  * ctx is NULL); never NULL. */
 const char* hom_last_error(const hom_ctx* ctx);
