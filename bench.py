@@ -64,13 +64,16 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+KINETIC_SOURCES = ["hom_fft.cuh", "hom_pass.cuh", "hom_kern.inc", "hom_kern_c64.cu"]
+
+
 def kernel_hash() -> str:
+    """Hash of the sources that define the kinetic passes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1903_02581_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".inc", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in KINETIC_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
