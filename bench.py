@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--inner", type=int, default=INNER)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     return ap.parse_args()
 
 
@@ -172,6 +173,49 @@ def oracle_sample_rate(steps: int = 1):
     return pts * steps / sec, sec, desc
 
 
+def precision_study(device: str):
+    """FP32 vs FP64 on the sweep32 workload (6 simulations, 32x32 per electron,
+    1000 steps): time to solution and error of P_b, norm and energy against
+    the FP64 oracle's stored observables (tests/golden/sweep32_oracle.json,
+    written by tests/golden/make_golden.py from the oracle only)."""
+    import torch
+
+    from paper_1903_02581_gb300 import binding as H
+    from paper_1903_02581_gb300 import workloads as W
+
+    path = os.path.join(ROOT, "tests", "golden", "sweep32_oracle.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)
+    out = {"workload": "sweep32: 6 simulations x 32x32 per electron (1,048,576 points each), 1000 steps",
+           "reference": "FP64 oracle (numpy) observables after 1000 steps"}
+    for prec in ("c64", "c128"):
+        w = W.sweep32(prec=prec)
+        pr = H.Propagator(w, device=device)
+        o0 = pr.observables()
+        pr.step(1)                       # warm-up (graph capture, module load)
+        pr.close()
+        pr = H.Propagator(w, device=device)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr.step(w["nsteps"])
+        obs = pr.observables()
+        sec = time.perf_counter() - t0
+        pts = (w["nx"] * w["ny"]) ** 2 * len(w["sims"])
+        errs = [abs(o["p_bunch"] - g["obs"]["1000"]["p_bunch"]) for o, g in zip(obs, gold["sims"])]
+        nd = [abs(o["norm"] - 1.0) for o in obs]
+        ed = [abs(o["energy"] - a["energy"]) / abs(a["energy"]) for o, a in zip(obs, o0)]
+        eo = [abs(o["energy"] - g["obs"]["1000"]["energy"]) / abs(g["obs"]["1000"]["energy"])
+              for o, g in zip(obs, gold["sims"])]
+        out[prec] = {"seconds": sec, "updates_per_s": pts * w["nsteps"] / sec,
+                     "max_abs_p_bunch_err_vs_oracle": max(errs), "max_norm_drift": max(nd),
+                     "max_rel_energy_drift": max(ed), "max_rel_energy_err_vs_oracle": max(eo)}
+        pr.close()
+    out["fp32_speedup"] = out["c64"]["updates_per_s"] / out["c128"]["updates_per_s"]
+    return out
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -264,16 +308,19 @@ def gb300_arm(args):
 
     # dominant kernel and its roofline (algorithmic bytes: 1 read + 1 write of the state per pass)
     algo_bytes = batch * pts * 8 * 2
-    k_row = prof["ms_row"] / max(prof["n_row"], 1)
-    k_col = prof["ms_col"] / max(prof["n_col"], 1)
-    name, avg_ms = ("kinetic_pass_col", k_col) if prof["ms_col"] >= prof["ms_row"] else ("kinetic_pass_row", k_row)
+    k_tr = prof["ms_transposing"] / max(prof["n_transposing"], 1)
+    k_ip = prof["ms_in_place"] / max(prof["n_in_place"], 1)
+    if prof["ms_transposing"] >= prof["ms_in_place"]:
+        name, avg_ms = "kinetic_pass_t", k_tr
+    else:
+        name, avg_ms = "kinetic_pass", k_ip
     peak, peak_kind = load_peaks()
     achieved = algo_bytes / (avg_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(name), "kernel": name, "peak_source": peak_kind,
-                "row_pass_ms": k_row, "col_pass_ms": k_col,
-                "row_pass_frac": algo_bytes / (k_row / 1000.0) / 1e9 / peak,
-                "col_pass_frac": algo_bytes / (k_col / 1000.0) / 1e9 / peak}
+                "transposing_pass_ms": k_tr, "in_place_pass_ms": k_ip,
+                "transposing_pass_frac": algo_bytes / (k_tr / 1000.0) / 1e9 / peak,
+                "in_place_pass_frac": algo_bytes / (k_ip / 1000.0) / 1e9 / peak}
 
     # end to end through the C ABI: host state in pinned memory copied in every step
     e2e = None
@@ -304,6 +351,10 @@ def gb300_arm(args):
         cpu = {"value": rate, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
                "seconds": sec}
 
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        precision = precision_study(f"cuda:{local}")
+
     launches = args.steps * (2 * args.inner + 4)
     if rank == 0:
         line = {
@@ -316,7 +367,7 @@ def gb300_arm(args):
                        "observables_per_step": 1, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (2 GiB state), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "p_bunch_last": obs[0]["p_bunch"] if obs else None,
+            "clocks": clocks, "precision": precision, "p_bunch_last": obs[0]["p_bunch"] if obs else None,
             "norm_last": obs[0]["norm"] if obs else None,
         }
         print(json.dumps(line), flush=True)

@@ -93,8 +93,11 @@ typedef struct hom_ctx hom_ctx;
  * 0 for invalid parameters. */
 size_t hom_state_bytes(const hom_params* p);
 
-/* Bytes of device workspace hom_create needs (tables, reduction partials,
- * packet buffers, ckpt_slots checkpoints).  Returns 0 for invalid parameters. */
+/* Bytes of device workspace hom_create needs: one state-sized buffer (each
+ * Strang step writes the transposed state psi[b][r2][r1] there between its two
+ * passes, so that both passes read contiguous planes), the phase tables,
+ * reduction partials, packet buffers and ckpt_slots checkpoints (plus one
+ * adjoint state when ckpt_slots > 0).  Returns 0 for invalid parameters. */
 size_t hom_workspace_bytes(const hom_params* p);
 
 /* Create a context.  d_state (hom_state_bytes) and d_workspace
@@ -121,7 +124,11 @@ hom_status hom_init_packets(hom_ctx* ctx, int32_t b, const hom_packet* alpha,
                             const hom_packet* beta, int32_t exch);
 
 /* Advance every simulation by nsteps Strang steps (nsteps >= 0), state in
- * real space before and after.  Asynchronous on the context's stream. */
+ * real space and in the layout above before and after.  Each step is two
+ * passes over the state (one per particle); the launches of a call are
+ * captured into a CUDA graph per step count and replayed (not on the legacy
+ * default stream, not while profiling, not while the caller captures the
+ * stream).  Asynchronous on the context's stream. */
 hom_status hom_step(hom_ctx* ctx, int32_t nsteps);
 
 /* Compute the observables of every simulation; out has batch entries (host).
@@ -152,14 +159,14 @@ hom_status hom_copy_state(hom_ctx* ctx, int32_t b, void* host, size_t bytes,
                           int32_t to_device);
 
 /* Instrumentation.  While enabled, hom_step records a pair of CUDA events on
- * the context's stream around every kinetic-pass launch (row pass: particle 2,
- * column pass: particle 1); hom_profile_read synchronises the stream and
- * returns the summed device milliseconds and launch counts of each pass since
- * the last enable.  Enabling resets the sums.  Costs two event records per
- * launch; no effect on results. */
+ * the context's stream around every kinetic-pass launch (transposing pass:
+ * the first of each step; in-place pass: the second) and launches without a
+ * CUDA graph; hom_profile_read synchronises the stream and returns the summed
+ * device milliseconds and launch counts of each kind since the last enable.
+ * Enabling resets the sums.  No effect on results. */
 hom_status hom_profile(hom_ctx* ctx, int32_t enable);
-hom_status hom_profile_read(hom_ctx* ctx, double* ms_row, double* ms_col, int64_t* n_row,
-                            int64_t* n_col);
+hom_status hom_profile_read(hom_ctx* ctx, double* ms_transposing, double* ms_in_place,
+                            int64_t* n_transposing, int64_t* n_in_place);
 
 /* Norm and bunching probability of a batch of states, for callers that
  * cannot allocate device memory: code that was handed the state in a buffer

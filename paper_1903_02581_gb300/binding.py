@@ -164,7 +164,7 @@ def hom_profile_read(ctx) -> dict:
     mr, mc = ctypes.c_double(), ctypes.c_double()
     nr, nc = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().hom_profile_read(ctx, ctypes.byref(mr), ctypes.byref(mc), ctypes.byref(nr), ctypes.byref(nc)), ctx)
-    return dict(ms_row=mr.value, ms_col=mc.value, n_row=nr.value, n_col=nc.value)
+    return dict(ms_transposing=mr.value, ms_in_place=mc.value, n_transposing=nr.value, n_in_place=nc.value)
 
 
 def hom_last_error(ctx) -> str:

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -69,7 +70,7 @@ struct Layout {
   size_t part_row, part_col, obs;
   size_t packets, dbeta, coef, exch, scratch;
   size_t adj_slot1, adj_slot2, adj_dv, adj_cdc, adj_out;
-  size_t lam, ckpt;
+  size_t lam, ckpt, pong;
   size_t total;
   int tiles_row, tiles_col;
 };
@@ -162,6 +163,7 @@ Layout make_layout(const hom_params& p) {
   L.adj_out = take(B * 4 * 8);
   L.lam = take(p.ckpt_slots > 0 ? B * n * n * eb : 0);
   L.ckpt = take((size_t)p.ckpt_slots * B * n * n * eb);
+  L.pong = take(B * n * n * eb);
   L.total = o;
   return L;
 }
@@ -185,10 +187,13 @@ struct hom_ctx {
   // instrumentation (hom_profile)
   bool prof;
   std::vector<cudaEvent_t> ev;     // event pool
-  std::vector<int> ev_kind;        // per recorded pair: 0 row, 1 col
+  std::vector<int> ev_kind;        // per recorded pair: 0 transposing pass, 1 in-place pass
   size_t ev_used;
   double prof_ms[2];
   long long prof_n[2];
+  // CUDA graphs of the forward step sequence, one per step count
+  bool use_graphs;
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
 };
 
 namespace {
@@ -433,36 +438,85 @@ hom_status prof_end(hom_ctx* c, size_t idx, int kind) {
   return HOM_OK;
 }
 
+// One Strang step = two kinetic passes, one per particle (their sandwiches
+// commute, so either goes first).  The state lives in psi = psi[r1][r2]
+// (layout A) or, between steps, in the workspace buffer as psi[r2][r1]
+// (layout B).  The first pass of a step reads the rows of the layout that
+// holds the state (the planes of one particle) and writes them transposed
+// into the other layout, whose rows are the other particle's planes; the
+// second pass works in place there.  So the state alternates between the two
+// layouts from step to step, each step costs one transposed store, and an
+// even number of steps ends in layout A (an odd number ends with a second
+// transposing pass back to A).  The potential phase (dt/2 on the first step,
+// dt after: the halves of neighbouring steps fused) is applied on the first
+// load of every step, the closing dt/2 on the last store.
 template <typename T>
 hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   using C = typename hom::Cx<T>::type;
   const hom_params& p = c->p;
-  hom::PassArgs<C> a{};
-  a.psi = reinterpret_cast<C*>(psi);
-  a.qa = reinterpret_cast<const C*>(c->ws + c->L.qa[sgn]);
-  a.qt = reinterpret_cast<const C*>(c->ws + c->L.qt[sgn]);
-  a.gy = reinterpret_cast<const C*>(c->ws + c->L.gy[sgn]);
-  a.twx = reinterpret_cast<const C*>(c->ws + c->L.twx);
-  a.twy = reinterpret_cast<const C*>(c->ws + c->L.twy);
+  const C* qa = reinterpret_cast<const C*>(c->ws + c->L.qa[sgn]);
+  const C* qt = reinterpret_cast<const C*>(c->ws + c->L.qt[sgn]);
+  const C* gy = reinterpret_cast<const C*>(c->ws + c->L.gy[sgn]);
+  const C* twx = reinterpret_cast<const C*>(c->ws + c->L.twx);
+  const C* twy = reinterpret_cast<const C*>(c->ws + c->L.twy);
   const C* p1h = reinterpret_cast<const C*>(c->ws + c->L.p1h[sgn]);
   const C* p1f = reinterpret_cast<const C*>(c->ws + c->L.p1f[sgn]);
   const C* p12h = reinterpret_cast<const C*>(c->ws + c->L.p12h[sgn]);
   const C* p12f = reinterpret_cast<const C*>(c->ws + c->L.p12f[sgn]);
-  for (int s = 0; s < nsteps; ++s) {
+  C* A = reinterpret_cast<C*>(psi);
+  C* Bp = reinterpret_cast<C*>(c->ws + c->L.pong);
+  bool in_a = true;
+  auto transposing = [&](C* src, C* dst, int v_load, int v_store, const C* t1, const C* t12) -> hom_status {
+    hom::PassArgsT<C> a{};
+    a.src = src;
+    a.dst = dst;
+    a.qa = qa;
+    a.qt = qt;
+    a.gy = gy;
+    a.twx = twx;
+    a.twy = twy;
+    a.p1 = t1;
+    a.p12 = t12;
+    a.v_load = v_load;
+    a.v_store = v_store;
     size_t ev = 0;
     hom_status st;
-    a.apply_v = 1;
-    a.p1 = s == 0 ? p1h : p1f;
-    a.p12 = s == 0 ? p12h : p12f;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
-    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, false, a, p.batch, c->stream)));
+    HOM_CUDA(c, (hom::launch_kinetic_t<T>(p.nx, p.ny, a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 0)) != HOM_OK) return st;
-    a.apply_v = s == nsteps - 1;
-    a.p1 = p1h;
-    a.p12 = p12h;
+    return HOM_OK;
+  };
+  auto in_place = [&](C* buf, int v_store, const C* t1, const C* t12) -> hom_status {
+    hom::PassArgs<C> a{};
+    a.psi = buf;
+    a.qa = qa;
+    a.qt = qt;
+    a.gy = gy;
+    a.twx = twx;
+    a.twy = twy;
+    a.p1 = t1;
+    a.p12 = t12;
+    a.v_load = 0;
+    a.v_store = v_store;
+    size_t ev = 0;
+    hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
-    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, true, a, p.batch, c->stream)));
+    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 1)) != HOM_OK) return st;
+    return HOM_OK;
+  };
+  for (int s = 0; s < nsteps; ++s) {
+    const bool last = s == nsteps - 1;
+    hom_status st = transposing(in_a ? A : Bp, in_a ? Bp : A, 1, 0, s == 0 ? p1h : p1f, s == 0 ? p12h : p12f);
+    if (st != HOM_OK) return st;
+    in_a = !in_a;
+    if (last && !in_a) {
+      st = transposing(Bp, A, 0, 1, p1h, p12h);
+      in_a = true;
+    } else {
+      st = in_place(in_a ? A : Bp, last ? 1 : 0, p1h, p12h);
+    }
+    if (st != HOM_OK) return st;
   }
   return HOM_OK;
 }
@@ -470,6 +524,41 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
 hom_status run_steps(hom_ctx* c, char* psi, int nsteps, int sgn) {
   return c->p.prec == HOM_C128 ? step_sequence<double>(c, psi, nsteps, sgn)
                                : step_sequence<float>(c, psi, nsteps, sgn);
+}
+
+constexpr size_t kMaxGraphs = 8;
+
+void drop_graphs(hom_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  c->graphs.clear();
+}
+
+// The forward sequence of nsteps steps on the state as one CUDA graph: the
+// 2*nsteps kinetic-pass launches are captured once per step count and
+// replayed with a single launch.
+hom_status run_steps_graph(hom_ctx* c, int nsteps) {
+  for (auto& g : c->graphs)
+    if (g.first == nsteps) {
+      HOM_CUDA(c, cudaGraphLaunch(g.second, c->stream));
+      return HOM_OK;
+    }
+  if (c->graphs.size() >= kMaxGraphs) drop_graphs(c);
+  HOM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  hom_status s = run_steps(c, c->state, nsteps, 0);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (s != HOM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(c, HOM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c, HOM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  c->graphs.emplace_back(nsteps, exec);
+  HOM_CUDA(c, cudaGraphLaunch(exec, c->stream));
+  return HOM_OK;
 }
 
 template <typename T>
@@ -537,6 +626,10 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
   c->ev_used = 0;
   c->prof_ms[0] = c->prof_ms[1] = 0.0;
   c->prof_n[0] = c->prof_n[1] = 0;
+  {
+    const char* g = getenv("HOM_GRAPHS");
+    c->use_graphs = !(g && g[0] == '0');
+  }
   c->sims.assign(p->batch, SimParams{p->qpc_h, p->qpc_w, p->coul_lambda});
   c->have_packets.assign(p->batch, 0);
   c->exch.assign(p->batch, -1);
@@ -544,6 +637,11 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
   if (e != cudaSuccess) {
     delete c;
     return fail(nullptr, HOM_ERR_CUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+  }
+  e = p->prec == HOM_C128 ? hom::prepare_kinetic<double>(p->nx, p->ny) : hom::prepare_kinetic<float>(p->nx, p->ny);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, HOM_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e));
   }
   hom_status s = build_shared_tables(c);
   for (int b = 0; s == HOM_OK && b < p->batch; ++b) s = build_sim_tables(c, b);
@@ -631,6 +729,14 @@ hom_status hom_step(hom_ctx* c, int32_t nsteps) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if (nsteps < 0) return fail(c, HOM_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return HOM_OK;
+  // graphs need a stream that can be captured (not the legacy default stream)
+  if (c->use_graphs && !c->prof && c->stream != nullptr && c->stream != cudaStreamLegacy) {
+    // not while the caller is itself capturing the stream
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HOM_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) return run_steps_graph(c, nsteps);
+  }
   return run_steps(c, c->state, nsteps, 0);
 }
 
@@ -790,19 +896,21 @@ hom_status hom_profile(hom_ctx* c, int32_t enable) {
   return HOM_OK;
 }
 
-hom_status hom_profile_read(hom_ctx* c, double* ms_row, double* ms_col, int64_t* n_row, int64_t* n_col) {
+hom_status hom_profile_read(hom_ctx* c, double* ms_transposing, double* ms_in_place, int64_t* n_transposing,
+                            int64_t* n_in_place) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if ((s = harvest_events(c)) != HOM_OK) return s;
-  if (ms_row) *ms_row = c->prof_ms[0];
-  if (ms_col) *ms_col = c->prof_ms[1];
-  if (n_row) *n_row = c->prof_n[0];
-  if (n_col) *n_col = c->prof_n[1];
+  if (ms_transposing) *ms_transposing = c->prof_ms[0];
+  if (ms_in_place) *ms_in_place = c->prof_ms[1];
+  if (n_transposing) *n_transposing = c->prof_n[0];
+  if (n_in_place) *n_in_place = c->prof_n[1];
   return HOM_OK;
 }
 
 void hom_destroy(hom_ctx* c) {
   if (!c) return;
+  drop_graphs(c);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   delete c;

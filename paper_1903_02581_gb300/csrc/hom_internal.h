@@ -20,9 +20,18 @@ struct GeoInfo {
 // G = 0 if (nx, ny) is not a supported size.
 template <typename T> GeoInfo geo_info(int nx, int ny, bool col);
 
+// Set the kernel attributes (dynamic shared memory, occupancy query) of the
+// kinetic passes of a grid on the current device, so that later launches,
+// including launches captured into a CUDA graph, make no attribute calls.
+template <typename T> cudaError_t prepare_kinetic(int nx, int ny);
+
+// In-place pass on rows (kinetic_pass).
 template <typename T>
-cudaError_t launch_kinetic(int nx, int ny, bool col, const PassArgs<typename Cx<T>::type>& a, int batch,
-                           cudaStream_t s);
+cudaError_t launch_kinetic(int nx, int ny, const PassArgs<typename Cx<T>::type>& a, int batch, cudaStream_t s);
+
+// Transposing pass (kinetic_pass_t).
+template <typename T>
+cudaError_t launch_kinetic_t(int nx, int ny, const PassArgsT<typename Cx<T>::type>& a, int batch, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_measure(int nx, int ny, bool col, const MeasureArgs<typename Cx<T>::type>& a, int batch,

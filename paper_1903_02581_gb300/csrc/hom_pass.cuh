@@ -8,12 +8,16 @@
 // F_{x1,x2} = F_{x1} F_{x2}, T_x = T_x1 + T_x2 (Appendix A):
 //   K = K_1 K_2,  K_i = F_xi^-1 Q_i F_yi^-1 G_i F_yi Q_i F_xi,
 //   Q_i = e^{-i dt/4 (k_xi - B y_i)^2},  G_i = e^{-i dt/2 k_yi^2}.
-// K_2 acts on the contiguous (x2, y2) plane of each fixed (x1, y1): the
-// "row pass"; K_1 acts on the (x1, y1) plane of each fixed (x2, y2), whose
-// elements are n = nx*ny apart: the "column pass".  The real-space phase
-// e^{-iV tau} (V1(r1) + V1(r2) + V12) is fused into the load of the row pass
-// and, for the last half step, into the store of the column pass.  Each pass
-// reads and writes the state once: two HBM round trips per step.
+// K_2 acts on the (x2, y2) plane of each fixed (x1, y1): a contiguous row of
+// psi[r1][r2]; K_1 acts on the (x1, y1) planes, the rows of the transposed
+// state psi[r2][r1].  Since K_1 and K_2 commute, a step applies them in either
+// order: its first pass reads rows of whichever layout holds the state and
+// writes the transposed layout (kinetic_pass_t), its second pass works in
+// place on the rows of that layout (kinetic_pass).  The real-space phase
+// e^{-iV tau} (V1(r1) + V1(r2) + V12, symmetric in the particles) is fused
+// into the first load of a step and, for the last half step, into the last
+// store.  Each pass reads and writes the state once: two HBM round trips per
+// step.
 //
 // A CTA holds G planes of one simulation in shared memory, laid out
 // [g][x][y] with row stride RS = ny + 1 and plane stride PS (padding chosen so
@@ -38,8 +42,28 @@ template <typename C> struct PassArgs {
   const C* twy;        // e^{-2 pi i j / ny}, j < ny: hi parts, then lo parts
   const C* p1;         // e^{-i tau V1(r)} - 1                 [batch][n]   (tau = dt/2 or dt)
   const C* p12;        // e^{-i tau V12(dx, dy)} - 1           [batch][(2nx-1)(2ny-1)]
-  int apply_v;         // row pass: phase at load; column pass: phase at store
-  int pref_ahead;      // row pass: prefetch into L2 the tile this many CTAs ahead (0: off)
+  int v_load;          // apply the potential phase when loading
+  int v_store;         // apply the potential phase when storing
+  int pref_ahead;      // prefetch into L2 the tile this many CTAs ahead (0: off)
+};
+
+// Transposing pass: reads G contiguous rows of src ([n][n] per simulation,
+// row = the plane of one particle for a fixed coordinate of the other) and
+// writes the result transposed into dst, so that the next pass again reads
+// contiguous rows (the state alternates between psi[r1][r2] and psi[r2][r1]).
+template <typename C> struct PassArgsT {
+  const C* src;
+  C* dst;
+  const C* qa;
+  const C* qt;
+  const C* gy;
+  const C* twx;
+  const C* twy;
+  const C* p1;
+  const C* p12;
+  int v_load;          // apply the potential phase when loading
+  int v_store;         // apply the potential phase when storing
+  int pref_ahead;      // prefetch into L2 the tile this many CTAs ahead (0: off)
 };
 
 template <typename C> struct MeasureArgs {
@@ -68,14 +92,17 @@ template <typename T, int NX, int NY, bool COL> struct Geo {
   static constexpr int PSM = (G >= LW) ? 1 : (LW / G);
   static constexpr int PS = PS0 + ((((PSM - PS0) % LW) + LW) % LW);
   static constexpr int ELEMS = G * PS;
-  static constexpr int NT = (G * N >= 8192) ? 512 : 256;
+#ifndef HOM_BIG_TILE_THREADS
+#define HOM_BIG_TILE_THREADS 512
+#endif
+  static constexpr int NT = (G * N >= 8192) ? HOM_BIG_TILE_THREADS : 256;
   static constexpr size_t SMEM = (size_t)(ELEMS + 2 * NX + 2 * NY) * sizeof(C);
   static constexpr int TILES_PER_SIM = N / G;
   static_assert(N % G == 0, "tile");
-  // Column pass with fewer than 4 planes per CTA: a cluster of CL CTAs owns
-  // CL*G adjacent columns, so that its loads and stores cover whole 32-byte
-  // sectors of each row; planes move between the CTAs through distributed
-  // shared memory.
+  // Transposing pass with fewer than 4 planes per CTA: a cluster of CL CTAs
+  // holds CL*G adjacent planes, so that its transposed stores cover whole
+  // 32-byte sectors; values move between the CTAs through distributed shared
+  // memory.
   static constexpr int CL = (COL && G < 4) ? 4 / G : 1;
   static_assert(TILES_PER_SIM % CL == 0, "cluster");
 };
@@ -131,52 +158,6 @@ __device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
       dft_reg<N2, false>(v);
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) line[(N2 * k1 + k2) * RS] = hook(N2 * k1 + k2, y, v[k2]);
-    }
-    __syncthreads();
-  }
-}
-
-// Inverse DFT along x (no 1/nx), digit-transposed positions in, natural out.
-template <typename C, int NX, int NY, int G, int NT, int RS, int PS>
-__device__ __forceinline__ void x_inverse(C* sm, const C* tw) {
-  using S = Split<NX>;
-  constexpr int N1 = S::N1, N2 = S::N2;
-  const int tid = threadIdx.x;
-  if constexpr (N2 == 1) {
-    for (int it = tid; it < G * NY; it += NT) {
-      const int y = it % NY, g = it / NY;
-      C* line = sm + g * PS + y;
-      C v[NX];
-#pragma unroll
-      for (int k = 0; k < NX; ++k) v[k] = line[k * RS];
-      dft_reg<NX, true>(v);
-#pragma unroll
-      for (int x = 0; x < NX; ++x) line[x * RS] = v[x];
-    }
-    __syncthreads();
-  } else {
-    for (int it = tid; it < G * NY * N1; it += NT) {
-      const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
-      C* line = sm + g * PS + y;
-      C v[N2];
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[(N2 * k1 + k2) * RS];
-      dft_reg<N2, true>(v);
-#pragma unroll
-      for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_hl<true>(v[m1], tw[m1 * k1], tw[NX + m1 * k1]);
-#pragma unroll
-      for (int m1 = 0; m1 < N2; ++m1) line[(N2 * k1 + m1) * RS] = v[m1];
-    }
-    __syncthreads();
-    for (int it = tid; it < G * NY * N2; it += NT) {
-      const int y = it % NY, m1 = (it / NY) % N2, g = it / (NY * N2);
-      C* line = sm + g * PS + y;
-      C v[N1];
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[(N2 * k1 + m1) * RS];
-      dft_reg<N1, true>(v);
-#pragma unroll
-      for (int m2 = 0; m2 < N1; ++m2) line[(m1 + N2 * m2) * RS] = v[m2];
     }
     __syncthreads();
   }
@@ -323,18 +304,181 @@ struct QHook {
 };
 
 // ---------------------------------------------------------------------------
-// Kinetic pass: row (COL = false, particle 2) or column (COL = true, particle 1).
+// Kinetic passes: in place on rows (kinetic_pass) or transposing (kinetic_pass_t).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <typename T, int NX, int NY, bool COL>
-__global__ void __launch_bounds__(Geo<T, NX, NY, COL>::NT)
+// Item decode of the stages that touch global memory: rows (lanes run over y,
+// contiguous in a row plane) or columns (lanes run over the G planes first,
+// which are the contiguous index of a column tile).
+template <bool COL, int NY, int G, int NSUB>
+__device__ __forceinline__ void decode_item(int it, int& g, int& y, int& sub) {
+  if constexpr (!COL) {
+    y = it % NY;
+    sub = (it / NY) % NSUB;
+    g = it / (NY * NSUB);
+  } else {
+    g = it % G;
+    y = (it / G) % NY;
+    sub = it / (G * NY);
+  }
+}
+
+template <bool COL, int NX, int NY>
+__device__ __forceinline__ size_t global_offset(int t0, int g, int x, int y) {
+  constexpr int N = NX * NY;
+  if constexpr (!COL) return (size_t)(t0 + g) * N + x * NY + y;
+  else return (size_t)(x * NY + y) * N + (t0 + g);
+}
+
+// First x stage read straight from global memory: every thread loads the N1
+// elements of its line segment (all in flight at once), applies the potential
+// phase if asked (it is symmetric in the two particles, so the plane index
+// t0 + g and the element index may be either particle's), transforms, and
+// writes shared memory.  With nx <= 16 this
+// is the whole forward x transform, followed by the T_x/2 hook.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL, class Hook>
+__device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const C* __restrict__ base, int t0,
+                                                      const C* __restrict__ p1, const C* __restrict__ p12,
+                                                      bool apply_v, Hook& hook) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  for (int it = threadIdx.x; it < G * NY * N2; it += NT) {
+    int g, y, n2;
+    decode_item<COL, NY, G, N2>(it, g, y, n2);
+    C v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = base[global_offset<COL, NX, NY>(t0, g, N2 * n1 + n2, y)];
+    if (apply_v) {
+      C d[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) d[n1] = vphase_delta<C, NX, NY>(p1, p12, t0 + g, (N2 * n1 + n2) * NY + y);
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = apply_delta(v[n1], d[n1]);
+    }
+    dft_reg<N1, false>(v);
+    C* line = sm + g * PS + y;
+    if constexpr (N2 == 1) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
+    } else {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NX + n2 * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + n2) * RS] = v[k1];
+    }
+  }
+  __syncthreads();
+}
+
+// Second forward x stage (shared memory only, nx > 16), hook on every output.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, class Hook>
+__device__ __forceinline__ void x_forward_second(C* sm, Hook& hook) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  for (int it = threadIdx.x; it < G * NY * N1; it += NT) {
+    const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
+    C* line = sm + g * PS + y;
+    C v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = line[(N2 * k1 + n2) * RS];
+    dft_reg<N2, false>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) line[(N2 * k1 + k2) * RS] = hook(N2 * k1 + k2, y, v[k2]);
+  }
+  __syncthreads();
+}
+
+// First inverse x stage (shared memory only, nx > 16).
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS>
+__device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  for (int it = threadIdx.x; it < G * NY * N1; it += NT) {
+    const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
+    C* line = sm + g * PS + y;
+    C v[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[(N2 * k1 + k2) * RS];
+    dft_reg<N2, true>(v);
+#pragma unroll
+    for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_hl<true>(v[m1], tw[m1 * k1], tw[NX + m1 * k1]);
+#pragma unroll
+    for (int m1 = 0; m1 < N2; ++m1) line[(N2 * k1 + m1) * RS] = v[m1];
+  }
+  __syncthreads();
+}
+
+// Last inverse x stage written straight to global memory (the whole inverse
+// x transform when nx <= 16), with the closing potential phase if asked.
+// COL = false writes the planes back as rows; COL = true writes them
+// transposed (element (x, y) of plane t0 + g to row x*ny + y, column t0 + g).
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL>
+__device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__ base, int t0,
+                                                    const C* __restrict__ p1, const C* __restrict__ p12,
+                                                    bool apply_v) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  for (int it = threadIdx.x; it < G * NY * N2; it += NT) {
+    int g, y, m1;
+    decode_item<COL, NY, G, N2>(it, g, y, m1);
+    const C* line = sm + g * PS + y;
+    C v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[(N2 * k1 + m1) * RS];
+    dft_reg<N1, true>(v);
+    if (apply_v) {
+#pragma unroll
+      for (int m2 = 0; m2 < N1; ++m2)
+        v[m2] = apply_delta(v[m2], vphase_delta<C, NX, NY>(p1, p12, (m1 + N2 * m2) * NY + y, t0 + g));
+    }
+#pragma unroll
+    for (int m2 = 0; m2 < N1; ++m2) base[global_offset<COL, NX, NY>(t0, g, m1 + N2 * m2, y)] = v[m2];
+  }
+}
+
+// Transposed store of a cluster of CL CTAs holding W = CL*G adjacent planes:
+// CTA q gathers, for every plane, the inputs of the last inverse x stage of
+// the lines m1 = q (mod CL) from the owning CTA (distributed shared memory),
+// transforms, applies the closing potential phase if asked, and writes
+// 32-byte segments (the W planes' values of one element) to the transposed
+// layout.  The caller synchronises the cluster before and after.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, int CL>
+__device__ __forceinline__ void x_inverse_cluster_store(const C* sm, C* __restrict__ base, int c0, int q,
+                                                        const C* __restrict__ p1, const C* __restrict__ p12,
+                                                        bool apply_v) {
+  namespace cg = cooperative_groups;
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2, N = NX * NY, W = CL * G;
+  cg::cluster_group cl = cg::this_cluster();
+  for (int it = threadIdx.x; it < W * NY * (N2 / CL); it += NT) {
+    const int j = it % W, y = (it / W) % NY, m1 = q + CL * (it / (W * NY));
+    const C* src = cl.map_shared_rank(const_cast<C*>(sm), j / G) + (j % G) * PS + y;
+    C v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(N2 * k1 + m1) * RS];
+    dft_reg<N1, true>(v);
+    if (apply_v) {
+#pragma unroll
+      for (int m2 = 0; m2 < N1; ++m2)
+        v[m2] = apply_delta(v[m2], vphase_delta<C, NX, NY>(p1, p12, (m1 + N2 * m2) * NY + y, c0 + j));
+    }
+#pragma unroll
+    for (int m2 = 0; m2 < N1; ++m2) base[(size_t)((m1 + N2 * m2) * NY + y) * N + c0 + j] = v[m2];
+  }
+}
+
+// In-place pass: one kinetic sandwich on G contiguous rows of psi (the plane
+// of one particle for a fixed coordinate of the other), written back in place.
+template <typename T, int NX, int NY>
+__global__ void __launch_bounds__(Geo<T, NX, NY, false>::NT)
 kinetic_pass(PassArgs<typename Cx<T>::type> a) {
-  using Gm = Geo<T, NX, NY, COL>;
+  using Gm = Geo<T, NX, NY, false>;
   using C = typename Cx<T>::type;
-  constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS, CL = Gm::CL;
+  constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
+  constexpr int N2X = Split<NX>::N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* stwx = sm + Gm::ELEMS;
@@ -349,76 +493,75 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   C* base = a.psi + (size_t)b * N * N;
   const C* p1 = a.p1 + (size_t)b * N;
   const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
-
-  if constexpr (!COL) {
-    // rows: G contiguous planes; start the HBM read of a later tile into L2
-    if (tid == 0 && a.pref_ahead > 0 && tile + a.pref_ahead < (int)gridDim.x) {
-      const int nt = tile + a.pref_ahead;
-      const C* p = a.psi + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
-      prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
-    }
-    for (int e = tid; e < G * N; e += NT) {
-      const int g = e / N, r = e % N;
-      C v = base[(size_t)(t0 + g) * N + r];
-      if (a.apply_v) v = apply_delta(v, vphase_delta<C, NX, NY>(p1, p12, t0 + g, r));
-      sm[g * PS + (r / NY) * RS + (r % NY)] = v;
-    }
-    __syncthreads();
-  } else if constexpr (CL == 1) {
-    for (int e = tid; e < G * N; e += NT) {
-      const int g = e % G, r = e / G;
-      sm[g * PS + (r / NY) * RS + (r % NY)] = base[(size_t)r * N + (t0 + g)];
-    }
-    __syncthreads();
-  } else {
-    // cluster: this CTA loads rows [q N/CL, (q+1) N/CL) of the cluster's CL*G
-    // columns and deals each element to the CTA owning its column
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const int q = (int)cl.block_rank();
-    const int c0 = t0 - q * G;
-    constexpr int W = CL * G, ROWS = N / CL;
-    cl.sync();                                   // every CTA of the cluster is running
-    for (int e = tid; e < ROWS * W; e += NT) {
-      const int j = e % W, r = q * ROWS + e / W;
-      const C v = base[(size_t)r * N + c0 + j];
-      C* dst = cl.map_shared_rank(sm, j / G);
-      dst[(j % G) * PS + (r / NY) * RS + (r % NY)] = v;
-    }
-    cl.sync();
-  }
-
   QHook<C, NY> qa{a.qa};
-  x_forward<C, NX, NY, G, NT, RS, PS>(sm, stwx, qa);
-  y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
-  x_inverse<C, NX, NY, G, NT, RS, PS>(sm, stwx);
 
-  if constexpr (!COL) {
-    for (int e = tid; e < G * N; e += NT) {
-      const int g = e / N, r = e % N;
-      base[(size_t)(t0 + g) * N + r] = sm[g * PS + (r / NY) * RS + (r % NY)];
-    }
-  } else if constexpr (CL == 1) {
-    for (int e = tid; e < G * N; e += NT) {
-      const int g = e % G, r = e / G;
-      C v = sm[g * PS + (r / NY) * RS + (r % NY)];
-      if (a.apply_v) v = apply_delta(v, vphase_delta<C, NX, NY>(p1, p12, r, t0 + g));
-      base[(size_t)r * N + (t0 + g)] = v;
-    }
+  // start the HBM read of the tile one wave later into L2
+  if (tid == 0 && a.pref_ahead > 0 && tile + a.pref_ahead < (int)gridDim.x) {
+    const int nt = tile + a.pref_ahead;
+    const C* p = a.psi + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
+    prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
+  }
+  __syncthreads();                               // twiddles in shared memory
+  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false>(sm, stwx, base, t0, p1, p12, a.v_load != 0, qa);
+  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
+  y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
+  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+  x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false>(sm, base, t0, p1, p12, a.v_store != 0);
+}
+
+#ifndef HOM_TSTORE_CLUSTER
+#define HOM_TSTORE_CLUSTER 1
+#endif
+
+// One kinetic sandwich of the particle whose plane is a row of src, written
+// transposed to dst (see PassArgsT).  The potential phase is symmetric in the
+// two particles, so the same kernel serves both particles.
+template <typename T, int NX, int NY>
+__global__ void __launch_bounds__(Geo<T, NX, NY, true>::NT)
+kinetic_pass_t(PassArgsT<typename Cx<T>::type> a) {
+  using Gm = Geo<T, NX, NY, true>;
+  using C = typename Cx<T>::type;
+  constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
+  constexpr int CL = HOM_TSTORE_CLUSTER ? Gm::CL : 1;
+  constexpr int N2X = Split<NX>::N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  C* stwx = sm + Gm::ELEMS;
+  C* stwy = stwx + 2 * NX;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
+  for (int i = tid; i < 2 * NY; i += NT) stwy[i] = a.twy[i];
+
+  const int tile = blockIdx.x;
+  const int b = tile / Gm::TILES_PER_SIM;
+  const int t0 = (tile % Gm::TILES_PER_SIM) * G;
+  const C* src = a.src + (size_t)b * N * N;
+  C* dst = a.dst + (size_t)b * N * N;
+  const C* p1 = a.p1 + (size_t)b * N;
+  const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
+  QHook<C, NY> qa{a.qa};
+
+  if (tid == 0 && a.pref_ahead > 0 && tile + a.pref_ahead < (int)gridDim.x) {
+    const int nt = tile + a.pref_ahead;
+    const C* p = a.src + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
+    prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
+  }
+  __syncthreads();                               // twiddles in shared memory
+  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false>(sm, stwx, src, t0, p1, p12, a.v_load != 0, qa);
+  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
+  y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
+  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+  if constexpr (CL == 1) {
+    // G >= 4 adjacent rows: the transposed store writes G*8-byte segments
+    x_inverse_to_global<C, NX, NY, G, NT, RS, PS, true>(sm, dst, t0, p1, p12, a.v_store != 0);
   } else {
+    // a cluster of CL CTAs holds CL*G adjacent rows: each CTA stores its share
+    // of all of them as 32-byte segments, read through distributed shared memory
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int q = (int)cl.block_rank();
-    const int c0 = t0 - q * G;
-    constexpr int W = CL * G, ROWS = N / CL;
-    cl.sync();                                   // every CTA has finished its planes
-    for (int e = tid; e < ROWS * W; e += NT) {
-      const int j = e % W, r = q * ROWS + e / W;
-      const C* src = cl.map_shared_rank(sm, j / G);
-      C v = src[(j % G) * PS + (r / NY) * RS + (r % NY)];
-      if (a.apply_v) v = apply_delta(v, vphase_delta<C, NX, NY>(p1, p12, r, c0 + j));
-      base[(size_t)r * N + c0 + j] = v;
-    }
+    cl.sync();
+    x_inverse_cluster_store<C, NX, NY, G, NT, RS, PS, CL>(sm, dst, t0 - q * G, q, p1, p12, a.v_store != 0);
     cl.sync();                                   // keep this CTA's planes alive for the readers
   }
 }

@@ -31,7 +31,8 @@ def test_state_and_workspace_sizes(lib):
     p64 = H.make_params(W.fullscale())
     assert H.hom_state_bytes(p64) == (256 * 64) ** 2 * 8
     ws = H.hom_workspace_bytes(p64)
-    assert 0 < ws < 64 * 2 ** 20          # tables and partials only, no state-sized scratch
+    state = (256 * 64) ** 2 * 8
+    assert state < ws < state + 64 * 2 ** 20      # one transposed state plus tables and partials
     p64.ckpt_slots = 2
     assert H.hom_workspace_bytes(p64) >= ws + 2 * (256 * 64) ** 2 * 8
 

@@ -1,0 +1,51 @@
+"""The sweep32 workload (6 simulations, 32x32 per electron, 1000 steps) in
+complex128 and complex64 against the FP64 oracle's stored observables
+(tests/golden/sweep32_oracle.json, written by make_golden.py from the oracle
+only).  Tolerances: complex128 P_b, norm and energy to 1e-10; complex64 P_b to
+1e-6 and norm to 1e-5 after 1000 steps."""
+
+import json
+import os
+
+import pytest
+
+from paper_1903_02581_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "sweep32_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def gold():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(GOLD):
+        pytest.skip("golden observables not generated")
+    from paper_1903_02581_gb300 import build
+
+    build.build()
+    with open(GOLD) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_sweep32_matches_oracle_observables(gold, prec):
+    from paper_1903_02581_gb300 import binding as H
+
+    w = W.sweep32(prec=prec)
+    pr = H.Propagator(w)
+    done = 0
+    for c in gold["checkpoints"]:
+        pr.step(c - done)
+        done = c
+        obs = pr.observables()
+        for o, g in zip(obs, gold["sims"]):
+            ref = g["obs"][str(c)]
+            if prec == "c128":
+                for k in ("norm", "energy", "e_kin", "e_pot", "e_coul", "p_bunch"):
+                    assert abs(o[k] - ref[k]) <= 1e-10 * max(1.0, abs(ref[k])), (c, k, o[k], ref[k])
+            else:
+                assert abs(o["p_bunch"] - ref["p_bunch"]) <= 1e-6, (c, o["p_bunch"], ref["p_bunch"])
+                assert abs(o["norm"] - ref["norm"]) <= 1e-5, (c, o["norm"])
