@@ -204,12 +204,15 @@ def precision_study(device: str):
         sec = time.perf_counter() - t0
         pts = (w["nx"] * w["ny"]) ** 2 * len(w["sims"])
         errs = [abs(o["p_bunch"] - g["obs"]["1000"]["p_bunch"]) for o, g in zip(obs, gold["sims"])]
+        errs_n = [abs(o["p_bunch"] / o["norm"] - g["obs"]["1000"]["p_bunch"] / g["obs"]["1000"]["norm"])
+                  for o, g in zip(obs, gold["sims"])]
         nd = [abs(o["norm"] - 1.0) for o in obs]
         ed = [abs(o["energy"] - a["energy"]) / abs(a["energy"]) for o, a in zip(obs, o0)]
         eo = [abs(o["energy"] - g["obs"]["1000"]["energy"]) / abs(g["obs"]["1000"]["energy"])
               for o, g in zip(obs, gold["sims"])]
         out[prec] = {"seconds": sec, "updates_per_s": pts * w["nsteps"] / sec,
-                     "max_abs_p_bunch_err_vs_oracle": max(errs), "max_norm_drift": max(nd),
+                     "max_abs_p_bunch_err_vs_oracle": max(errs),
+                     "max_abs_normalised_p_bunch_err_vs_oracle": max(errs_n), "max_norm_drift": max(nd),
                      "max_rel_energy_drift": max(ed), "max_rel_energy_err_vs_oracle": max(eo)}
         pr.close()
     out["fp32_speedup"] = out["c64"]["updates_per_s"] / out["c128"]["updates_per_s"]
@@ -297,6 +300,7 @@ def gb300_arm(args):
         dist.barrier()
     torch.cuda.synchronize()
     prof = H.hom_profile_read(pr.ctx)
+    tuning = H.hom_autotune_info(pr.ctx)
     H.hom_profile(pr.ctx, False)
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
@@ -320,7 +324,8 @@ def gb300_arm(args):
                 "traffic": ncu_traffic(name), "kernel": name, "peak_source": peak_kind,
                 "transposing_pass_ms": k_tr, "in_place_pass_ms": k_ip,
                 "transposing_pass_frac": algo_bytes / (k_tr / 1000.0) / 1e9 / peak,
-                "in_place_pass_frac": algo_bytes / (k_ip / 1000.0) / 1e9 / peak}
+                "in_place_pass_frac": algo_bytes / (k_ip / 1000.0) / 1e9 / peak,
+                "autotune": tuning}
 
     # end to end through the C ABI: host state in pinned memory copied in every step
     e2e = None

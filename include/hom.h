@@ -168,6 +168,17 @@ hom_status hom_profile(hom_ctx* ctx, int32_t enable);
 hom_status hom_profile_read(hom_ctx* ctx, double* ms_transposing, double* ms_in_place,
                             int64_t* n_transposing, int64_t* n_in_place);
 
+/* Autotuner.  Each kinetic pass has two kernel variants that differ only in
+ * thread count or cluster width (transposing pass: 4- or 2-plane clusters
+ * for large planes), so results are bitwise identical whichever runs.  The
+ * first hom_step call with at least 16 steps times both variants on its first
+ * 8 steps (CUDA events around every launch) and keeps the faster variant of
+ * each pass for the context (disabled, variant 0 always, if the environment
+ * variable HOM_TUNE is "0").  variants[2] (transposing, in-place) receives
+ * the chosen variants, -1 before tuning; ms[4], if not NULL, the timed device
+ * milliseconds [pass kind * 2 + variant]. */
+hom_status hom_autotune_info(hom_ctx* ctx, int32_t* variants, double* ms);
+
 /* Norm and bunching probability of a batch of states, for callers that
  * cannot allocate device memory: code that was handed the state in a buffer
  * it does not own (another framework's tensor, a slice of a pool) and runs

@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
     L.hom_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64),
                                    P(ctypes.c_int64)]
     L.hom_profile_read.restype = ctypes.c_int
+    L.hom_autotune_info.argtypes = [vp, P(ctypes.c_int32), P(ctypes.c_double)]
+    L.hom_autotune_info.restype = ctypes.c_int
     L.hom_last_error.argtypes = [vp]
     L.hom_last_error.restype = ctypes.c_char_p
     L.hom_destroy.argtypes = [vp]
@@ -165,6 +167,13 @@ def hom_profile_read(ctx) -> dict:
     nr, nc = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().hom_profile_read(ctx, ctypes.byref(mr), ctypes.byref(mc), ctypes.byref(nr), ctypes.byref(nc)), ctx)
     return dict(ms_transposing=mr.value, ms_in_place=mc.value, n_transposing=nr.value, n_in_place=nc.value)
+
+
+def hom_autotune_info(ctx) -> dict:
+    v = (ctypes.c_int32 * 2)()
+    ms = (ctypes.c_double * 4)()
+    _check(lib().hom_autotune_info(ctx, v, ms), ctx)
+    return dict(variants=list(v), ms=list(ms))
 
 
 def hom_last_error(ctx) -> str:

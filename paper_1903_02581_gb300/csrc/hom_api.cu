@@ -5,13 +5,14 @@
 // Paper: arXiv:1903.02581, Sec. II.C (Eq. evoloperat, Landau-gauge
 // Hamiltonian), Appendix A (Eq. 2PTB), Eq. coulomb, Eq. twopstate,
 // Eq. singlepwp, Eq. p_bunching.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
-#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -193,6 +194,14 @@ struct hom_ctx {
   long long prof_n[2];
   // CUDA graphs of the forward step sequence, one per step count
   bool use_graphs;
+  // autotuner: kernel variant of the transposing [0] and in-place [1] passes
+  int variant[2];
+  bool tuned;
+  bool tune_enabled;
+  double tune_ms[2][2];   // [pass kind][variant], device ms of a timed 2-step run
+  // tensor maps of the buffers a transposing pass writes (state, transposed
+  // buffer, adjoint state), per kernel variant; used where tma_store_width > 0
+  CUtensorMap maps[3][2];
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
 };
 
@@ -468,6 +477,9 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   bool in_a = true;
   auto transposing = [&](C* src, C* dst, int v_load, int v_store, const C* t1, const C* t12) -> hom_status {
     hom::PassArgsT<C> a{};
+    const char* d = reinterpret_cast<const char*>(dst);
+    const int bi = d == c->state ? 0 : (d == c->ws + c->L.pong ? 1 : 2);
+    a.tmap_dst = c->maps[bi][c->variant[0]];
     a.src = src;
     a.dst = dst;
     a.qa = qa;
@@ -482,7 +494,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     size_t ev = 0;
     hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
-    HOM_CUDA(c, (hom::launch_kinetic_t<T>(p.nx, p.ny, a, p.batch, c->stream)));
+    HOM_CUDA(c, (hom::launch_kinetic_t<T>(p.nx, p.ny, c->variant[0], a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 0)) != HOM_OK) return st;
     return HOM_OK;
   };
@@ -501,7 +513,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     size_t ev = 0;
     hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
-    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, a, p.batch, c->stream)));
+    HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, c->variant[1], a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 1)) != HOM_OK) return st;
     return HOM_OK;
   };
@@ -521,9 +533,52 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   return HOM_OK;
 }
 
+// nsteps steps on psi with time step +dt (sgn 0) or -dt (sgn 1).
 hom_status run_steps(hom_ctx* c, char* psi, int nsteps, int sgn) {
   return c->p.prec == HOM_C128 ? step_sequence<double>(c, psi, nsteps, sgn)
                                : step_sequence<float>(c, psi, nsteps, sgn);
+}
+
+// Autotuner: the kernel variants of a pass (Geo, variant 0 or 1) differ only
+// in thread counts and cluster widths, so every element of the state sees the
+// same arithmetic and the results are bitwise identical.  The first forward
+// hom_step call with at least kTuneMinSteps steps runs, for each variant, two
+// steps to warm up and two timed steps (CUDA events around every launch) on
+// the real state; the faster variant of each pass kind is kept for the
+// context.  Those steps are part of the requested steps.
+constexpr int kTuneMinSteps = 16;
+
+hom_status autotune(hom_ctx* c) {
+  const bool prof_saved = c->prof;
+  const double ms_saved[2] = {c->prof_ms[0], c->prof_ms[1]};
+  const long long n_saved[2] = {c->prof_n[0], c->prof_n[1]};
+  hom_status s;
+  if ((s = harvest_events(c)) != HOM_OK) return s;
+  if (c->ev.empty()) {
+    c->ev.resize(kEventPool, nullptr);
+    for (auto& e : c->ev) HOM_CUDA(c, cudaEventCreate(&e));
+  }
+  for (int v = 0; v < 2; ++v) {
+    c->variant[0] = c->variant[1] = v;
+    c->prof = false;
+    if ((s = run_steps(c, c->state, 2, 0)) != HOM_OK) return s;
+    c->prof = true;
+    c->prof_ms[0] = c->prof_ms[1] = 0.0;
+    c->prof_n[0] = c->prof_n[1] = 0;
+    if ((s = run_steps(c, c->state, 2, 0)) != HOM_OK) return s;
+    if ((s = harvest_events(c)) != HOM_OK) return s;
+    c->tune_ms[0][v] = c->prof_ms[0];
+    c->tune_ms[1][v] = c->prof_ms[1];
+  }
+  c->variant[0] = c->tune_ms[0][1] < c->tune_ms[0][0] ? 1 : 0;
+  c->variant[1] = c->tune_ms[1][1] < c->tune_ms[1][0] ? 1 : 0;
+  c->prof = prof_saved;
+  c->prof_ms[0] = ms_saved[0];
+  c->prof_ms[1] = ms_saved[1];
+  c->prof_n[0] = n_saved[0];
+  c->prof_n[1] = n_saved[1];
+  c->tuned = true;
+  return HOM_OK;
 }
 
 constexpr size_t kMaxGraphs = 8;
@@ -558,6 +613,48 @@ hom_status run_steps_graph(hom_ctx* c, int nsteps) {
   if (e != cudaSuccess) return fail(c, HOM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
   c->graphs.emplace_back(nsteps, exec);
   HOM_CUDA(c, cudaGraphLaunch(exec, c->stream));
+  return HOM_OK;
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the
+// driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps for the transposed stores: each buffer seen as [batch*n rows]
+// [n columns] of 8-byte elements, box of w columns x ny rows.
+hom_status build_tensor_maps(hom_ctx* c) {
+  const hom_params& p = c->p;
+  std::memset(c->maps, 0, sizeof c->maps);
+  if (p.prec != HOM_C64) return HOM_OK;
+  const int w[2] = {hom::tma_store_width<float>(p.nx, p.ny, 0), hom::tma_store_width<float>(p.nx, p.ny, 1)};
+  if (w[0] == 0 && w[1] == 0) return HOM_OK;
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(c, HOM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t n = (cuuint64_t)p.nx * p.ny;
+  char* bufs[3] = {c->state, c->ws + c->L.pong, p.ckpt_slots > 0 ? c->ws + c->L.lam : nullptr};
+  for (int bi = 0; bi < 3; ++bi) {
+    if (!bufs[bi]) continue;
+    for (int v = 0; v < 2; ++v) {
+      if (w[v] == 0) continue;
+      const cuuint64_t dims[2] = {n, n * (cuuint64_t)p.batch};
+      const cuuint64_t strides[1] = {n * 8};
+      const cuuint32_t box[2] = {(cuuint32_t)w[v], (cuuint32_t)p.ny};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult r = encode(&c->maps[bi][v], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, bufs[bi], dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(c, HOM_ERR_CUDA, "tensor map encoding failed (%d)", (int)r);
+    }
+  }
   return HOM_OK;
 }
 
@@ -629,6 +726,11 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
   {
     const char* g = getenv("HOM_GRAPHS");
     c->use_graphs = !(g && g[0] == '0');
+    const char* tu = getenv("HOM_TUNE");
+    c->tune_enabled = !(tu && tu[0] == '0');
+    c->variant[0] = c->variant[1] = 0;
+    c->tuned = false;
+    for (auto& r : c->tune_ms) r[0] = r[1] = 0.0;
   }
   c->sims.assign(p->batch, SimParams{p->qpc_h, p->qpc_w, p->coul_lambda});
   c->have_packets.assign(p->batch, 0);
@@ -643,7 +745,8 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
     delete c;
     return fail(nullptr, HOM_ERR_CUDA, "kernel set-up failed: %s", cudaGetErrorString(e));
   }
-  hom_status s = build_shared_tables(c);
+  hom_status s = build_tensor_maps(c);
+  if (s == HOM_OK) s = build_shared_tables(c);
   for (int b = 0; s == HOM_OK && b < p->batch; ++b) s = build_sim_tables(c, b);
   if (s != HOM_OK) {
     g_create_error = c->err;
@@ -730,6 +833,15 @@ hom_status hom_step(hom_ctx* c, int32_t nsteps) {
   if (s != HOM_OK) return s;
   if (nsteps < 0) return fail(c, HOM_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return HOM_OK;
+  if (!c->tuned && c->tune_enabled && nsteps >= kTuneMinSteps) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HOM_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      if ((s = autotune(c)) != HOM_OK) return s;
+      nsteps -= 8;
+      drop_graphs(c);                            // graphs hold the variants they were captured with
+    }
+  }
   // graphs need a stream that can be captured (not the legacy default stream)
   if (c->use_graphs && !c->prof && c->stream != nullptr && c->stream != cudaStreamLegacy) {
     // not while the caller is itself capturing the stream
@@ -876,6 +988,19 @@ hom_status hom_copy_state(hom_ctx* c, int32_t b, void* host, size_t bytes, int32
 const char* hom_last_error(const hom_ctx* c) {
   if (!c) return g_create_error.c_str();
   return c->err.c_str();
+}
+
+hom_status hom_autotune_info(hom_ctx* c, int32_t* variants, double* ms) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (variants) {
+    variants[0] = c->tuned ? c->variant[0] : -1;
+    variants[1] = c->tuned ? c->variant[1] : -1;
+  }
+  if (ms)
+    for (int k = 0; k < 2; ++k)
+      for (int v = 0; v < 2; ++v) ms[2 * k + v] = c->tune_ms[k][v];
+  return HOM_OK;
 }
 
 hom_status hom_profile(hom_ctx* c, int32_t enable) {

@@ -25,13 +25,19 @@ template <typename T> GeoInfo geo_info(int nx, int ny, bool col);
 // including launches captured into a CUDA graph, make no attribute calls.
 template <typename T> cudaError_t prepare_kinetic(int nx, int ny);
 
-// In-place pass on rows (kinetic_pass).
+// In-place pass on rows (kinetic_pass), variant 0 or 1 (see Geo).
 template <typename T>
-cudaError_t launch_kinetic(int nx, int ny, const PassArgs<typename Cx<T>::type>& a, int batch, cudaStream_t s);
+cudaError_t launch_kinetic(int nx, int ny, int variant, const PassArgs<typename Cx<T>::type>& a, int batch,
+                           cudaStream_t s);
 
-// Transposing pass (kinetic_pass_t).
+// Transposing pass (kinetic_pass_t), variant 0 or 1.
 template <typename T>
-cudaError_t launch_kinetic_t(int nx, int ny, const PassArgsT<typename Cx<T>::type>& a, int batch, cudaStream_t s);
+cudaError_t launch_kinetic_t(int nx, int ny, int variant, const PassArgsT<typename Cx<T>::type>& a, int batch,
+                             cudaStream_t s);
+
+// Columns per transposed-store tile of the transposing pass of a grid (kernel
+// variant 0 or 1) when it stores through the tensor memory accelerator, else 0.
+template <typename T> int tma_store_width(int nx, int ny, int variant);
 
 template <typename T>
 cudaError_t launch_measure(int nx, int ny, bool col, const MeasureArgs<typename Cx<T>::type>& a, int batch,

@@ -25,6 +25,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +53,7 @@ template <typename C> struct PassArgs {
 // writes the result transposed into dst, so that the next pass again reads
 // contiguous rows (the state alternates between psi[r1][r2] and psi[r2][r1]).
 template <typename C> struct PassArgsT {
+  CUtensorMap tmap_dst;   // dst as [batch*n rows][n columns] of 8-byte elements (clustered complex64 pass)
   const C* src;
   C* dst;
   const C* qa;
@@ -79,7 +81,12 @@ template <typename C> struct MeasureArgs {
 
 constexpr int NPART = 6;   // norm, e_pot, e_coul, p_bunch, e_tx, e_ty (raw sums)
 
-template <typename T, int NX, int NY, bool COL> struct Geo {
+// Tile geometry.  COL = false: the in-place pass (G contiguous rows per CTA,
+// up to 32 KB of planes); COL = true: the transposing pass and the column
+// observables (up to 128 KB of planes, so that G >= 4 columns give 32-byte
+// segments).  V selects one of two variants the autotuner times (results are
+// identical; only thread counts and cluster widths differ).
+template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   using C = typename Cx<T>::type;
   static constexpr int N = NX * NY;
   static constexpr int LW = 128 / (int)sizeof(C);        // lanes per shared-memory wavefront
@@ -92,19 +99,29 @@ template <typename T, int NX, int NY, bool COL> struct Geo {
   static constexpr int PSM = (G >= LW) ? 1 : (LW / G);
   static constexpr int PS = PS0 + ((((PSM - PS0) % LW) + LW) % LW);
   static constexpr int ELEMS = G * PS;
-#ifndef HOM_BIG_TILE_THREADS
-#define HOM_BIG_TILE_THREADS 512
-#endif
-  static constexpr int NT = (G * N >= 8192) ? HOM_BIG_TILE_THREADS : 256;
   static constexpr size_t SMEM = (size_t)(ELEMS + 2 * NX + 2 * NY) * sizeof(C);
   static constexpr int TILES_PER_SIM = N / G;
   static_assert(N % G == 0, "tile");
   // Transposing pass with fewer than 4 planes per CTA: a cluster of CL CTAs
   // holds CL*G adjacent planes, so that its transposed stores cover whole
-  // 32-byte sectors; values move between the CTAs through distributed shared
-  // memory.
-  static constexpr int CL = (COL && G < 4) ? 4 / G : 1;
+  // 32-byte sectors (variant 1: half as wide, 16-byte segments); values move
+  // between the CTAs through distributed shared memory.
+  static constexpr int CL0 = (COL && G < 4) ? 4 / G : 1;
+  static constexpr int CL = (V == 1 && CL0 > 1) ? CL0 / 2 : CL0;
   static_assert(TILES_PER_SIM % CL == 0, "cluster");
+  // threads: 512 for complex64 tiles of 8192 points or more, else 256 (a
+  // complex128 thread holds twice the registers); variant 1 of an unclustered
+  // kernel uses the other count
+  static constexpr int NT0 = (sizeof(C) == 8 && G * N >= 8192) ? 512 : 256;
+  static constexpr int NT = (V == 1 && CL0 == 1) ? (NT0 == 512 ? 256 : 512) : NT0;
+  // clustered complex64 transposing pass: its stores go through the tensor
+  // memory accelerator from two staging buffers of N1 tiles of ny rows x CL*G
+  // columns (see x_inverse_cluster_store_tma)
+  static constexpr bool TMA_STORE = COL && CL > 1 && sizeof(C) == 8;
+  static constexpr int STAGE = TMA_STORE ? 2 * Split<NX>::N1 * NY * CL * G : 0;
+  static constexpr size_t STAGE_OFF = ((size_t)(ELEMS + 2 * NX + 2 * NY) * sizeof(C) + 127) / 128 * 128;
+  // + 128 bytes of slack: the kernel rounds the staging address up to 128 bytes
+  static constexpr size_t SMEM_ALL = TMA_STORE ? STAGE_OFF + (size_t)STAGE * sizeof(C) + 128 : SMEM;
 };
 
 // ---------------------------------------------------------------------------
@@ -472,10 +489,10 @@ __device__ __forceinline__ void x_inverse_cluster_store(const C* sm, C* __restri
 
 // In-place pass: one kinetic sandwich on G contiguous rows of psi (the plane
 // of one particle for a fixed coordinate of the other), written back in place.
-template <typename T, int NX, int NY>
-__global__ void __launch_bounds__(Geo<T, NX, NY, false>::NT)
+template <typename T, int NX, int NY, int V>
+__global__ void __launch_bounds__(Geo<T, NX, NY, false, V>::NT)
 kinetic_pass(PassArgs<typename Cx<T>::type> a) {
-  using Gm = Geo<T, NX, NY, false>;
+  using Gm = Geo<T, NX, NY, false, V>;
   using C = typename Cx<T>::type;
   constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
   constexpr int N2X = Split<NX>::N2;
@@ -509,20 +526,81 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false>(sm, base, t0, p1, p12, a.v_store != 0);
 }
 
-#ifndef HOM_TSTORE_CLUSTER
-#define HOM_TSTORE_CLUSTER 1
-#endif
-
 // One kinetic sandwich of the particle whose plane is a row of src, written
 // transposed to dst (see PassArgsT).  The potential phase is symmetric in the
 // two particles, so the same kernel serves both particles.
-template <typename T, int NX, int NY>
-__global__ void __launch_bounds__(Geo<T, NX, NY, true>::NT)
-kinetic_pass_t(PassArgsT<typename Cx<T>::type> a) {
-  using Gm = Geo<T, NX, NY, true>;
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* smem, int c0, int c1) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(c0),
+               "r"(c1), "r"(s)
+               : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void tma_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Transposed store of a cluster of CL CTAs through the tensor memory
+// accelerator.  CTA q handles the lines m1 = q (mod CL) in rounds of one m1:
+// for every plane j of the cluster and every y it gathers the N1 inputs of the
+// last inverse x stage from the owning CTA, transforms, applies the closing
+// potential phase if asked, and writes the N1 outputs (x = m1 + N2 m2) into a
+// staging buffer laid out as N1 tiles [y][j]; one thread then stores tile m2
+// to rows (row0 + x*ny .. + ny) and columns c0 .. c0 + W of the transposed
+// layout with one bulk tensor copy.  Two staging buffers alternate; a buffer is
+// rewritten only after the copies that read it have finished reading.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, int CL>
+__device__ __forceinline__ void x_inverse_cluster_store_tma(const C* sm, C* stage, const CUtensorMap* map, int row0,
+                                                            int c0, int q, const C* __restrict__ p1,
+                                                            const C* __restrict__ p12, bool apply_v) {
+  namespace cg = cooperative_groups;
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2, W = CL * G, TILE = NY * W;
+  cg::cluster_group cl = cg::this_cluster();
+  const int tid = threadIdx.x;
+  for (int s = 0; s < N2 / CL; ++s) {
+    const int m1 = q + CL * s;
+    C* st = stage + (s & 1) * (N1 * TILE);
+    if (s >= 2) {
+      if (tid == 0) tma_wait_read<1>();          // the copies of round s-2 have read this buffer
+      __syncthreads();
+    }
+    for (int it = tid; it < W * NY; it += NT) {
+      const int j = it % W, y = it / W;
+      const C* src = cl.map_shared_rank(const_cast<C*>(sm), j / G) + (j % G) * PS + y;
+      C v[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(N2 * k1 + m1) * RS];
+      dft_reg<N1, true>(v);
+      if (apply_v) {
+#pragma unroll
+        for (int m2 = 0; m2 < N1; ++m2)
+          v[m2] = apply_delta(v[m2], vphase_delta<C, NX, NY>(p1, p12, (m1 + N2 * m2) * NY + y, c0 + j));
+      }
+#pragma unroll
+      for (int m2 = 0; m2 < N1; ++m2) st[m2 * TILE + y * W + j] = v[m2];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      fence_proxy_async();                       // staging writes visible to the copy engine
+#pragma unroll 1
+      for (int m2 = 0; m2 < N1; ++m2) tma_store_2d(map, st + m2 * TILE, c0, row0 + (m1 + N2 * m2) * NY);
+      tma_commit();
+    }
+  }
+  if (tid == 0) tma_wait_all();                  // stores complete before the CTA's shared memory goes
+  __syncthreads();
+}
+
+template <typename T, int NX, int NY, int V>
+__global__ void __launch_bounds__(Geo<T, NX, NY, true, V>::NT)
+kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
+  using Gm = Geo<T, NX, NY, true, V>;
   using C = typename Cx<T>::type;
   constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
-  constexpr int CL = HOM_TSTORE_CLUSTER ? Gm::CL : 1;
+  constexpr int CL = Gm::CL;
   constexpr int N2X = Split<NX>::N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
@@ -561,7 +639,15 @@ kinetic_pass_t(PassArgsT<typename Cx<T>::type> a) {
     cg::cluster_group cl = cg::this_cluster();
     const int q = (int)cl.block_rank();
     cl.sync();
-    x_inverse_cluster_store<C, NX, NY, G, NT, RS, PS, CL>(sm, dst, t0 - q * G, q, p1, p12, a.v_store != 0);
+    if constexpr (Gm::TMA_STORE) {
+      // staging at a 128-byte aligned shared address (bulk tensor copies need it)
+      const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem_raw + Gm::STAGE_OFF);
+      C* stage = reinterpret_cast<C*>(smem_raw + Gm::STAGE_OFF + ((128u - (s0 & 127u)) & 127u));
+      x_inverse_cluster_store_tma<C, NX, NY, G, NT, RS, PS, CL>(sm, stage, &a.tmap_dst, b * N, t0 - q * G, q, p1,
+                                                                p12, a.v_store != 0);
+    } else {
+      x_inverse_cluster_store<C, NX, NY, G, NT, RS, PS, CL>(sm, dst, t0 - q * G, q, p1, p12, a.v_store != 0);
+    }
     cl.sync();                                   // keep this CTA's planes alive for the readers
   }
 }
