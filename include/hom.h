@@ -124,8 +124,9 @@ hom_status hom_init_packets(hom_ctx* ctx, int32_t b, const hom_packet* alpha,
                             const hom_packet* beta, int32_t exch);
 
 /* Advance every simulation by nsteps Strang steps (nsteps >= 0), state in
- * real space and in the layout above before and after.  Each step is two
- * passes over the state (one per particle); the launches of a call are
+ * real space and in the layout above before and after.  Each step applies
+ * one kinetic sandwich per particle (see hom_autotune_info for the two ways
+ * of sequencing them); the launches of a call are
  * captured into a CUDA graph per step count and replayed (not on the legacy
  * default stream, not while profiling, not while the caller captures the
  * stream).  Asynchronous on the context's stream. */
@@ -159,25 +160,32 @@ hom_status hom_copy_state(hom_ctx* ctx, int32_t b, void* host, size_t bytes,
                           int32_t to_device);
 
 /* Instrumentation.  While enabled, hom_step records a pair of CUDA events on
- * the context's stream around every kinetic-pass launch (transposing pass:
- * the first of each step; in-place pass: the second) and launches without a
- * CUDA graph; hom_profile_read synchronises the stream and returns the summed
- * device milliseconds and launch counts of each kind since the last enable.
- * Enabling resets the sums.  No effect on results. */
+ * the context's stream around every kernel launch of a step and launches
+ * without a CUDA graph; hom_profile_read synchronises the stream and returns,
+ * for the kinds [0] transposing pass, [1] in-place pass, [2] transpose, the
+ * summed device milliseconds (ms[3]) and launch counts (counts[3]) since the
+ * last enable.  Enabling resets the sums.  No effect on results. */
 hom_status hom_profile(hom_ctx* ctx, int32_t enable);
-hom_status hom_profile_read(hom_ctx* ctx, double* ms_transposing, double* ms_in_place,
-                            int64_t* n_transposing, int64_t* n_in_place);
+hom_status hom_profile_read(hom_ctx* ctx, double* ms, int64_t* counts);
 
-/* Autotuner.  Each kinetic pass has two kernel variants that differ only in
- * thread count or cluster width (transposing pass: 4- or 2-plane clusters
- * for large planes), so results are bitwise identical whichever runs.  The
- * first hom_step call with at least 16 steps times both variants on its first
- * 8 steps (CUDA events around every launch) and keeps the faster variant of
- * each pass for the context (disabled, variant 0 always, if the environment
- * variable HOM_TUNE is "0").  variants[2] (transposing, in-place) receives
- * the chosen variants, -1 before tuning; ms[4], if not NULL, the timed device
- * milliseconds [pass kind * 2 + variant]. */
-hom_status hom_autotune_info(hom_ctx* ctx, int32_t* variants, double* ms);
+/* Autotuner.  A step runs either strategy 0 (a transposing pass, then an
+ * in-place pass on the other layout) or strategy 1 (an in-place pass, a
+ * transpose, an in-place pass), and each kinetic pass has two kernel variants
+ * that differ only in thread count or cluster width.  Every choice applies the
+ * same arithmetic to every element, so results are bitwise identical.  The
+ * first hom_step call with at least 24 steps times the candidates on its first
+ * 12 steps (CUDA events around every launch) and keeps the fastest for the
+ * context (disabled, strategy 0 with variants 0, if the environment variable
+ * HOM_TUNE is "0").  choice[3] receives (transposing-pass variant, in-place
+ * variant, strategy), -1 before tuning; ms[6], if not NULL, the timed device
+ * milliseconds: [pass kind * 2 + variant] for the two kinds, then the step
+ * time of strategy 0 and of strategy 1. */
+hom_status hom_autotune_info(hom_ctx* ctx, int32_t* choice, double* ms);
+
+/* Fix the choice instead of tuning: choice[3] = (transposing-pass variant,
+ * in-place variant, strategy), each 0 or 1 (HOM_ERR_ARG otherwise).  Later
+ * hom_step calls use it and never tune.  Results do not depend on it. */
+hom_status hom_autotune_set(hom_ctx* ctx, const int32_t* choice);
 
 /* Norm and bunching probability of a batch of states, for callers that
  * cannot allocate device memory: code that was handed the state in a buffer

@@ -92,11 +92,12 @@ def lib() -> ctypes.CDLL:
     L.hom_copy_state.restype = ctypes.c_int
     L.hom_profile.argtypes = [vp, ctypes.c_int32]
     L.hom_profile.restype = ctypes.c_int
-    L.hom_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64),
-                                   P(ctypes.c_int64)]
+    L.hom_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64)]
     L.hom_profile_read.restype = ctypes.c_int
     L.hom_autotune_info.argtypes = [vp, P(ctypes.c_int32), P(ctypes.c_double)]
     L.hom_autotune_info.restype = ctypes.c_int
+    L.hom_autotune_set.argtypes = [vp, P(ctypes.c_int32)]
+    L.hom_autotune_set.restype = ctypes.c_int
     L.hom_last_error.argtypes = [vp]
     L.hom_last_error.restype = ctypes.c_char_p
     L.hom_destroy.argtypes = [vp]
@@ -163,17 +164,23 @@ def hom_profile(ctx, enable: bool):
 
 
 def hom_profile_read(ctx) -> dict:
-    mr, mc = ctypes.c_double(), ctypes.c_double()
-    nr, nc = ctypes.c_int64(), ctypes.c_int64()
-    _check(lib().hom_profile_read(ctx, ctypes.byref(mr), ctypes.byref(mc), ctypes.byref(nr), ctypes.byref(nc)), ctx)
-    return dict(ms_transposing=mr.value, ms_in_place=mc.value, n_transposing=nr.value, n_in_place=nc.value)
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(lib().hom_profile_read(ctx, ms, n), ctx)
+    return dict(ms_transposing=ms[0], ms_in_place=ms[1], ms_transpose=ms[2],
+                n_transposing=n[0], n_in_place=n[1], n_transpose=n[2])
 
 
 def hom_autotune_info(ctx) -> dict:
-    v = (ctypes.c_int32 * 2)()
-    ms = (ctypes.c_double * 4)()
+    v = (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_double * 6)()
     _check(lib().hom_autotune_info(ctx, v, ms), ctx)
-    return dict(variants=list(v), ms=list(ms))
+    return dict(variants=list(v[:2]), strategy=v[2], pass_ms=list(ms[:4]), step_ms=list(ms[4:]))
+
+
+def hom_autotune_set(ctx, variant_transposing: int, variant_in_place: int, strategy: int) -> None:
+    ch = (ctypes.c_int32 * 3)(variant_transposing, variant_in_place, strategy)
+    _check(lib().hom_autotune_set(ctx, ch), ctx)
 
 
 def hom_last_error(ctx) -> str:

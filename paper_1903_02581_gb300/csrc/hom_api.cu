@@ -188,17 +188,21 @@ struct hom_ctx {
   // instrumentation (hom_profile)
   bool prof;
   std::vector<cudaEvent_t> ev;     // event pool
-  std::vector<int> ev_kind;        // per recorded pair: 0 transposing pass, 1 in-place pass
+  std::vector<int> ev_kind;        // per recorded pair: kind (see kNumKinds)
   size_t ev_used;
-  double prof_ms[2];
-  long long prof_n[2];
+  double prof_ms[3];               // transposing pass, in-place pass, transpose
+  long long prof_n[3];
   // CUDA graphs of the forward step sequence, one per step count
   bool use_graphs;
-  // autotuner: kernel variant of the transposing [0] and in-place [1] passes
+  // autotuner: kernel variant of the transposing [0] and in-place [1] passes,
+  // and the step strategy (0: transposing pass + in-place pass; 1: in-place
+  // pass + transpose + in-place pass)
   int variant[2];
+  int strategy;
   bool tuned;
   bool tune_enabled;
   double tune_ms[2][2];   // [pass kind][variant], device ms of a timed 2-step run
+  double tune_step_ms[2]; // [strategy], device ms of a timed 2-step run
   // tensor maps of the buffers a transposing pass writes (state, transposed
   // buffer, adjoint state), per kernel variant; used where tma_store_width > 0
   CUtensorMap maps[3][2];
@@ -498,7 +502,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     if (c->prof && (st = prof_end(c, ev, 0)) != HOM_OK) return st;
     return HOM_OK;
   };
-  auto in_place = [&](C* buf, int v_store, const C* t1, const C* t12) -> hom_status {
+  auto in_place_v = [&](C* buf, int v_load, int v_store, const C* t1, const C* t12) -> hom_status {
     hom::PassArgs<C> a{};
     a.psi = buf;
     a.qa = qa;
@@ -508,7 +512,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     a.twy = twy;
     a.p1 = t1;
     a.p12 = t12;
-    a.v_load = 0;
+    a.v_load = v_load;
     a.v_store = v_store;
     size_t ev = 0;
     hom_status st;
@@ -517,6 +521,37 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     if (c->prof && (st = prof_end(c, ev, 1)) != HOM_OK) return st;
     return HOM_OK;
   };
+  auto in_place = [&](C* buf, int v_store, const C* t1, const C* t12) -> hom_status {
+    return in_place_v(buf, 0, v_store, t1, t12);
+  };
+  auto transpose = [&](C* src, C* dst) -> hom_status {
+    size_t ev = 0;
+    hom_status st;
+    if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    HOM_CUDA(c, (hom::launch_transpose<T>(src, dst, p.nx * p.ny, p.batch, c->stream)));
+    if (c->prof && (st = prof_end(c, ev, 2)) != HOM_OK) return st;
+    return HOM_OK;
+  };
+  if (c->strategy == 1) {
+    // in-place pass (potential phase at load), transpose, in-place pass
+    for (int s = 0; s < nsteps; ++s) {
+      const bool last = s == nsteps - 1;
+      C* cur = in_a ? A : Bp;
+      C* oth = in_a ? Bp : A;
+      hom_status st = in_place_v(cur, 1, 0, s == 0 ? p1h : p1f, s == 0 ? p12h : p12f);
+      if (st != HOM_OK) return st;
+      if ((st = transpose(cur, oth)) != HOM_OK) return st;
+      in_a = !in_a;
+      if (last && !in_a) {
+        // the other particle's sandwich on the way back to the caller's layout
+        if ((st = transposing(Bp, A, 0, 1, p1h, p12h)) != HOM_OK) return st;
+        in_a = true;
+      } else if ((st = in_place_v(oth, 0, last ? 1 : 0, p1h, p12h)) != HOM_OK) {
+        return st;
+      }
+    }
+    return HOM_OK;
+  }
   for (int s = 0; s < nsteps; ++s) {
     const bool last = s == nsteps - 1;
     hom_status st = transposing(in_a ? A : Bp, in_a ? Bp : A, 1, 0, s == 0 ? p1h : p1f, s == 0 ? p12h : p12f);
@@ -540,43 +575,67 @@ hom_status run_steps(hom_ctx* c, char* psi, int nsteps, int sgn) {
 }
 
 // Autotuner: the kernel variants of a pass (Geo, variant 0 or 1) differ only
-// in thread counts and cluster widths, so every element of the state sees the
+// in thread counts and cluster widths, and the two step strategies only in
+// where the transposition happens, so every element of the state sees the
 // same arithmetic and the results are bitwise identical.  The first forward
-// hom_step call with at least kTuneMinSteps steps runs, for each variant, two
+// hom_step call with at least kTuneMinSteps steps runs, for each variant
+// under strategy 0 and then for the better variants under strategy 1, two
 // steps to warm up and two timed steps (CUDA events around every launch) on
-// the real state; the faster variant of each pass kind is kept for the
-// context.  Those steps are part of the requested steps.
-constexpr int kTuneMinSteps = 16;
+// the real state; the fastest choice is kept for the context.  Those 12 steps
+// are part of the requested steps.
+constexpr int kTuneMinSteps = 24;
 
 hom_status autotune(hom_ctx* c) {
   const bool prof_saved = c->prof;
-  const double ms_saved[2] = {c->prof_ms[0], c->prof_ms[1]};
-  const long long n_saved[2] = {c->prof_n[0], c->prof_n[1]};
+  double ms_saved[3];
+  long long n_saved[3];
+  for (int k = 0; k < 3; ++k) {
+    ms_saved[k] = c->prof_ms[k];
+    n_saved[k] = c->prof_n[k];
+  }
   hom_status s;
   if ((s = harvest_events(c)) != HOM_OK) return s;
   if (c->ev.empty()) {
     c->ev.resize(kEventPool, nullptr);
     for (auto& e : c->ev) HOM_CUDA(c, cudaEventCreate(&e));
   }
-  for (int v = 0; v < 2; ++v) {
-    c->variant[0] = c->variant[1] = v;
+  // two untimed then two timed steps of a configuration; returns the kinds' ms
+  auto trial = [&](int strategy, int v0, int v1, double* ms) -> hom_status {
+    c->strategy = strategy;
+    c->variant[0] = v0;
+    c->variant[1] = v1;
     c->prof = false;
-    if ((s = run_steps(c, c->state, 2, 0)) != HOM_OK) return s;
+    hom_status st;
+    if ((st = run_steps(c, c->state, 2, 0)) != HOM_OK) return st;
     c->prof = true;
-    c->prof_ms[0] = c->prof_ms[1] = 0.0;
-    c->prof_n[0] = c->prof_n[1] = 0;
-    if ((s = run_steps(c, c->state, 2, 0)) != HOM_OK) return s;
-    if ((s = harvest_events(c)) != HOM_OK) return s;
-    c->tune_ms[0][v] = c->prof_ms[0];
-    c->tune_ms[1][v] = c->prof_ms[1];
+    for (int k = 0; k < 3; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_n[k] = 0;
+    }
+    if ((st = run_steps(c, c->state, 2, 0)) != HOM_OK) return st;
+    if ((st = harvest_events(c)) != HOM_OK) return st;
+    for (int k = 0; k < 3; ++k) ms[k] = c->prof_ms[k];
+    return HOM_OK;
+  };
+  double ms[3];
+  for (int v = 0; v < 2; ++v) {
+    if ((s = trial(0, v, v, ms)) != HOM_OK) return s;
+    c->tune_ms[0][v] = ms[0];
+    c->tune_ms[1][v] = ms[1];
   }
-  c->variant[0] = c->tune_ms[0][1] < c->tune_ms[0][0] ? 1 : 0;
-  c->variant[1] = c->tune_ms[1][1] < c->tune_ms[1][0] ? 1 : 0;
+  const int v0 = c->tune_ms[0][1] < c->tune_ms[0][0] ? 1 : 0;
+  const int v1 = c->tune_ms[1][1] < c->tune_ms[1][0] ? 1 : 0;
+  c->tune_step_ms[0] = c->tune_ms[0][v0] + c->tune_ms[1][v1];
+  if ((s = trial(1, v0, v1, ms)) != HOM_OK) return s;
+  c->tune_step_ms[1] = ms[1] + ms[2];
+  c->strategy = c->tune_step_ms[1] < c->tune_step_ms[0] ? 1 : 0;
+  c->variant[0] = v0;
+  c->variant[1] = v1;
   c->prof = prof_saved;
-  c->prof_ms[0] = ms_saved[0];
-  c->prof_ms[1] = ms_saved[1];
-  c->prof_n[0] = n_saved[0];
-  c->prof_n[1] = n_saved[1];
+  for (int k = 0; k < 3; ++k) {
+    c->prof_ms[k] = ms_saved[k];
+    c->prof_n[k] = n_saved[k];
+  }
   c->tuned = true;
   return HOM_OK;
 }
@@ -721,16 +780,20 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
   c->err = "no error";
   c->prof = false;
   c->ev_used = 0;
-  c->prof_ms[0] = c->prof_ms[1] = 0.0;
-  c->prof_n[0] = c->prof_n[1] = 0;
+  for (int k = 0; k < 3; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+  }
   {
     const char* g = getenv("HOM_GRAPHS");
     c->use_graphs = !(g && g[0] == '0');
     const char* tu = getenv("HOM_TUNE");
     c->tune_enabled = !(tu && tu[0] == '0');
     c->variant[0] = c->variant[1] = 0;
+    c->strategy = 0;
     c->tuned = false;
     for (auto& r : c->tune_ms) r[0] = r[1] = 0.0;
+    c->tune_step_ms[0] = c->tune_step_ms[1] = 0.0;
   }
   c->sims.assign(p->batch, SimParams{p->qpc_h, p->qpc_w, p->coul_lambda});
   c->have_packets.assign(p->batch, 0);
@@ -838,7 +901,7 @@ hom_status hom_step(hom_ctx* c, int32_t nsteps) {
     HOM_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
     if (cs == cudaStreamCaptureStatusNone) {
       if ((s = autotune(c)) != HOM_OK) return s;
-      nsteps -= 8;
+      nsteps -= 12;
       drop_graphs(c);                            // graphs hold the variants they were captured with
     }
   }
@@ -990,16 +1053,34 @@ const char* hom_last_error(const hom_ctx* c) {
   return c->err.c_str();
 }
 
-hom_status hom_autotune_info(hom_ctx* c, int32_t* variants, double* ms) {
+hom_status hom_autotune_set(hom_ctx* c, const int32_t* choice) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
-  if (variants) {
-    variants[0] = c->tuned ? c->variant[0] : -1;
-    variants[1] = c->tuned ? c->variant[1] : -1;
+  if (!choice) return fail(c, HOM_ERR_ARG, "choice is NULL");
+  for (int k = 0; k < 3; ++k)
+    if (choice[k] != 0 && choice[k] != 1) return fail(c, HOM_ERR_ARG, "autotune choices must be 0 or 1");
+  c->variant[0] = choice[0];
+  c->variant[1] = choice[1];
+  c->strategy = choice[2];
+  c->tuned = true;
+  drop_graphs(c);
+  return HOM_OK;
+}
+
+hom_status hom_autotune_info(hom_ctx* c, int32_t* choice, double* ms) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (choice) {
+    choice[0] = c->tuned ? c->variant[0] : -1;
+    choice[1] = c->tuned ? c->variant[1] : -1;
+    choice[2] = c->tuned ? c->strategy : -1;
   }
-  if (ms)
+  if (ms) {
     for (int k = 0; k < 2; ++k)
       for (int v = 0; v < 2; ++v) ms[2 * k + v] = c->tune_ms[k][v];
+    ms[4] = c->tune_step_ms[0];
+    ms[5] = c->tune_step_ms[1];
+  }
   return HOM_OK;
 }
 
@@ -1014,22 +1095,23 @@ hom_status hom_profile(hom_ctx* c, int32_t enable) {
     HOM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->ev_used = 0;
     c->ev_kind.clear();
-    c->prof_ms[0] = c->prof_ms[1] = 0.0;
-    c->prof_n[0] = c->prof_n[1] = 0;
+    for (int k = 0; k < 3; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_n[k] = 0;
+    }
   }
   c->prof = enable != 0;
   return HOM_OK;
 }
 
-hom_status hom_profile_read(hom_ctx* c, double* ms_transposing, double* ms_in_place, int64_t* n_transposing,
-                            int64_t* n_in_place) {
+hom_status hom_profile_read(hom_ctx* c, double* ms, int64_t* counts) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if ((s = harvest_events(c)) != HOM_OK) return s;
-  if (ms_transposing) *ms_transposing = c->prof_ms[0];
-  if (ms_in_place) *ms_in_place = c->prof_ms[1];
-  if (n_transposing) *n_transposing = c->prof_n[0];
-  if (n_in_place) *n_in_place = c->prof_n[1];
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (counts) counts[k] = c->prof_n[k];
+  }
   return HOM_OK;
 }
 

@@ -35,6 +35,10 @@ template <typename T>
 cudaError_t launch_kinetic_t(int nx, int ny, int variant, const PassArgsT<typename Cx<T>::type>& a, int batch,
                              cudaStream_t s);
 
+// dst = transpose of each [n][n] state of src (batch states).
+template <typename T>
+cudaError_t launch_transpose(const void* src, void* dst, int n, int batch, cudaStream_t s);
+
 // Columns per transposed-store tile of the transposing pass of a grid (kernel
 // variant 0 or 1) when it stores through the tensor memory accelerator, else 0.
 template <typename T> int tma_store_width(int nx, int ny, int variant);

@@ -652,6 +652,32 @@ kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
   }
 }
 
+// dst[b][c][r] = src[b][r][c] for a batch of [n][n] states: tiles of T x T
+// through shared memory (row stride T + 1: conflict-free column reads), rows
+// read and written as contiguous T-element segments.  Used between two
+// in-place passes by the second step strategy (see step_sequence).
+template <typename C, int T>
+__global__ void __launch_bounds__(256) transpose_state(const C* __restrict__ src, C* __restrict__ dst, int n,
+                                                       int batch) {
+  __shared__ C tile[T][T + 1];
+  constexpr int ROWS = 256 / T;
+  const int r0 = blockIdx.y * T, c0 = blockIdx.x * T;
+  const int tx = threadIdx.x % T, ty = threadIdx.x / T;
+  for (int b = blockIdx.z; b < batch; b += gridDim.z) {
+    const C* s = src + (size_t)b * n * n;
+    C* d = dst + (size_t)b * n * n;
+    C v[T / ROWS];
+#pragma unroll
+    for (int i = 0; i < T / ROWS; ++i) v[i] = s[(size_t)(r0 + ty + i * ROWS) * n + c0 + tx];
+    if (b != (int)blockIdx.z) __syncthreads();        // previous simulation's tile fully read
+#pragma unroll
+    for (int i = 0; i < T / ROWS; ++i) tile[ty + i * ROWS][tx] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < T / ROWS; ++i) d[(size_t)(c0 + ty + i * ROWS) * n + r0 + tx] = tile[tx][ty + i * ROWS];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Observables: raw sums per tile, FP64 accumulation.
 // ---------------------------------------------------------------------------
