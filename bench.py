@@ -65,7 +65,67 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-KINETIC_SOURCES = ["hom_fft.cuh", "hom_pass.cuh", "hom_kern.inc", "hom_kern_c64.cu"]
+def _dft_flops(n: int) -> int:
+    """FP32 flops of the in-register radix-2 DFT of length n (add, sub, mul = 1,
+    FMA = 2): butterflies cost 4, a trivial twiddle (1, -i) 0, a (1 -+ i)/sqrt2
+    twiddle 8 (two sums, two compensated scalings) and any other compensated
+    twiddle 14 (two products and two FMAs per component)."""
+    if n == 1:
+        return 0
+    if n == 2:
+        return 4
+    tw = 0
+    for k in range(1, n // 2):
+        if 4 * k == n:
+            continue
+        tw += 8 if 8 * k in (n, 3 * n) else 14
+    return 2 * _dft_flops(n // 2) + 4 * (n // 2) + tw
+
+
+def _split(n: int):
+    n1 = n if n <= 16 else (16 if n >= 128 else 8)
+    return n1, n // n1
+
+
+def sandwich_flops(nx: int, ny: int) -> float:
+    """Algorithmic FP32 flops per point of one kinetic sandwich as the kernels
+    compute it: the x and y DFT stages, the compensated inter-stage twiddles
+    (14), the T_x/2 and T_y phases applied as v + v*d (8 each) and the 1/(nx ny)
+    scale (2)."""
+    tw, ph = 14.0, 8.0
+    f = 0.0
+    n1, n2 = _split(nx)
+    if n2 == 1:
+        f += _dft_flops(nx) / nx + ph + _dft_flops(nx) / nx
+    else:
+        f += _dft_flops(n1) / n1 + tw * (n1 - 1) / n1 + _dft_flops(n2) / n2 + ph       # forward x, T_x/2
+        f += _dft_flops(n2) / n2 + tw * (n2 - 1) / n2 + _dft_flops(n1) / n1            # inverse x
+    m1, m2 = _split(ny)
+    if m2 == 1:
+        f += 2 * _dft_flops(ny) / ny + ph + 2 + ph
+    else:
+        f += _dft_flops(m1) / m1 + tw * (m1 - 1) / m1
+        f += 2 * _dft_flops(m2) / m2 + ph + tw * (m2 - 1) / m2
+        f += _dft_flops(m1) / m1 + 2 + ph
+    return f
+
+
+VPHASE_FLOPS = 22.0   # three deltas combined (two complex products, four adds) and applied
+
+
+def fp32_peak_tflops() -> float:
+    """Nominal FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
+    at the maximum SM clock of the GB300s."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+KINETIC_SOURCES = ["hom_fft.cuh", "hom_pass.cuh", "hom_kern.inc", "hom_kern_c64.cu", "hom_kern_c64_rows.cu"]
 
 
 def kernel_hash() -> str:
@@ -310,25 +370,41 @@ def gb300_arm(args):
     ms_max = float(ms_t.item())
     value = world * batch * pts * args.inner * args.steps / (ms_max / 1000.0)
 
-    # dominant kernel and its roofline (algorithmic bytes: 1 read + 1 write of the state per launch)
+    # dominant kernel and its roofline.  Algorithmic bytes: one read and one
+    # write of the state per launch.  Algorithmic FP32 flops: one kinetic
+    # sandwich per point (two plus the potential phase in the double pass).
     algo_bytes = batch * pts * 8 * 2
-    kinds = [("kinetic_pass_t", prof["ms_transposing"], prof["n_transposing"]),
-             ("kinetic_pass", prof["ms_in_place"], prof["n_in_place"]),
-             ("transpose_state", prof["ms_transpose"], prof["n_transpose"])]
-    name, tot_ms, cnt = max(kinds, key=lambda k: k[1])
-    avg_ms = tot_ms / max(cnt, 1)
+    sw = sandwich_flops(w["nx"], w["ny"])
+    kinds = [("kinetic_pass_t", prof["ms_transposing"], prof["n_transposing"], sw),
+             ("kinetic_pass", prof["ms_in_place"], prof["n_in_place"], sw),
+             ("transpose_state", prof["ms_transpose"], prof["n_transpose"], 0.0),
+             ("kinetic_pass_double", prof["ms_double"], prof["n_double"], 2 * sw + VPHASE_FLOPS)]
     peak, peak_kind = load_peaks()
-    achieved = algo_bytes / (avg_ms / 1000.0) / 1e9
-    per_kernel = {k: {"launches": c_, "avg_ms": t / max(c_, 1),
-                      "frac": (algo_bytes / (t / max(c_, 1) / 1000.0) / 1e9 / peak) if c_ else None}
-                  for k, t, c_ in kinds}
-    step_bytes = 2 * algo_bytes                      # algorithmic: 2 round trips per Strang step
-    step_ms = sum(t for _, t, _ in kinds) / max(args.steps * args.inner, 1)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(name), "kernel": name, "peak_source": peak_kind,
-                "kernels": per_kernel,
-                "step_algorithmic_frac": step_bytes / (step_ms / 1000.0) / 1e9 / peak,
-                "autotune": tuning}
+    fpeak = fp32_peak_tflops()
+    per_kernel = {}
+    for k, t, c_, fl in kinds:
+        if not c_:
+            continue
+        avg = t / c_ / 1000.0
+        per_kernel[k] = {"launches": c_, "avg_ms": avg * 1000.0,
+                         "hbm_gbs": algo_bytes / avg / 1e9, "hbm_frac": algo_bytes / avg / 1e9 / peak,
+                         "fp32_tflops": fl * batch * pts / avg / 1e12,
+                         "fp32_frac": fl * batch * pts / avg / 1e12 / fpeak,
+                         "flops_per_point": fl}
+    name, tot_ms, cnt, _ = max(kinds, key=lambda k: k[1])
+    dom = per_kernel[name]
+    if dom["fp32_frac"] > dom["hbm_frac"]:
+        roofline = {"bound": "alu", "achieved": dom["fp32_tflops"], "peak": fpeak, "unit": "TFLOP/s",
+                    "frac": dom["fp32_frac"], "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        roofline = {"bound": "hbm", "achieved": dom["hbm_gbs"], "peak": peak, "unit": "GB/s",
+                    "frac": dom["hbm_frac"], "peak_source": peak_kind}
+    step_ms = sum(k[1] for k in kinds) / max(args.steps * args.inner, 1)
+    roofline.update({"traffic": ncu_traffic(name), "kernel": name, "kernels": per_kernel,
+                     "hbm_peak_gbs": peak,
+                     # the two-round-trip floor: 32 B per point per step (complex64)
+                     "step_algorithmic_hbm_frac": 2 * algo_bytes / (step_ms / 1000.0) / 1e9 / peak,
+                     "step_ms": step_ms, "autotune": tuning})
 
     # end to end through the C ABI: host state in pinned memory copied in every step
     e2e = None

@@ -125,7 +125,7 @@ hom_status hom_init_packets(hom_ctx* ctx, int32_t b, const hom_packet* alpha,
 
 /* Advance every simulation by nsteps Strang steps (nsteps >= 0), state in
  * real space and in the layout above before and after.  Each step applies
- * one kinetic sandwich per particle (see hom_autotune_info for the two ways
+ * one kinetic sandwich per particle (see hom_autotune_info for the three ways
  * of sequencing them); the launches of a call are
  * captured into a CUDA graph per step count and replayed (not on the legacy
  * default stream, not while profiling, not while the caller captures the
@@ -162,28 +162,38 @@ hom_status hom_copy_state(hom_ctx* ctx, int32_t b, void* host, size_t bytes,
 /* Instrumentation.  While enabled, hom_step records a pair of CUDA events on
  * the context's stream around every kernel launch of a step and launches
  * without a CUDA graph; hom_profile_read synchronises the stream and returns,
- * for the kinds [0] transposing pass, [1] in-place pass, [2] transpose, the
- * summed device milliseconds (ms[3]) and launch counts (counts[3]) since the
- * last enable.  Enabling resets the sums.  No effect on results. */
+ * for each launch kind, the summed device milliseconds (ms[HOM_PROFILE_KINDS])
+ * and launch counts (counts[HOM_PROFILE_KINDS]) since the last enable.  The
+ * kinds are [0] transposing pass, [1] in-place pass, [2] transpose, [3]
+ * double in-place pass.  Enabling resets the sums.  No effect on results. */
+#define HOM_PROFILE_KINDS 4
 hom_status hom_profile(hom_ctx* ctx, int32_t enable);
 hom_status hom_profile_read(hom_ctx* ctx, double* ms, int64_t* counts);
 
-/* Autotuner.  A step runs either strategy 0 (a transposing pass, then an
- * in-place pass on the other layout) or strategy 1 (an in-place pass, a
- * transpose, an in-place pass), and each kinetic pass has two kernel variants
- * that differ only in thread count or cluster width.  Every choice applies the
- * same arithmetic to every element, so results are bitwise identical.  The
- * first hom_step call with at least 24 steps times the candidates on its first
- * 12 steps (CUDA events around every launch) and keeps the fastest for the
+/* Autotuner.  A step applies one kinetic sandwich per particle, and the
+ * second particle's sandwich needs the state transposed.  Three strategies
+ * sequence the passes:
+ *   0: a transposing pass, then an in-place pass on the other layout;
+ *   1: an in-place pass, a transpose, an in-place pass;
+ *   2: a transpose and one double in-place pass per step, the double pass
+ *      holding the end of one step, the potential phase between steps and
+ *      the start of the next (same particle, same layout).
+ * Each kinetic pass also has two kernel variants that differ only in thread
+ * count or cluster width.  Every choice applies the same arithmetic to every
+ * element in the same order, so results are bitwise identical.  The first
+ * hom_step call with at least 24 steps times the candidates on its first 12
+ * steps (CUDA events around every launch) and keeps the fastest for the
  * context (disabled, strategy 0 with variants 0, if the environment variable
  * HOM_TUNE is "0").  choice[3] receives (transposing-pass variant, in-place
- * variant, strategy), -1 before tuning; ms[6], if not NULL, the timed device
- * milliseconds: [pass kind * 2 + variant] for the two kinds, then the step
- * time of strategy 0 and of strategy 1. */
+ * variant, strategy), -1 before tuning; ms[7], if not NULL, the measured
+ * device milliseconds per launch [pass kind * 2 + variant] of the
+ * transposing (kind 0) and in-place (kind 1) passes, then the estimated
+ * milliseconds per step of strategies 0, 1 and 2. */
 hom_status hom_autotune_info(hom_ctx* ctx, int32_t* choice, double* ms);
 
 /* Fix the choice instead of tuning: choice[3] = (transposing-pass variant,
- * in-place variant, strategy), each 0 or 1 (HOM_ERR_ARG otherwise).  Later
+ * in-place variant, strategy), variants 0 or 1, strategy 0, 1 or 2
+ * (HOM_ERR_ARG otherwise).  Later
  * hom_step calls use it and never tune.  Results do not depend on it. */
 hom_status hom_autotune_set(hom_ctx* ctx, const int32_t* choice);
 

@@ -163,17 +163,25 @@ def hom_profile(ctx, enable: bool):
     _check(lib().hom_profile(ctx, 1 if enable else 0), ctx)
 
 
+HOM_PROFILE_KINDS = 4
+PROFILE_KINDS = ("transposing", "in_place", "transpose", "double")
+
+
 def hom_profile_read(ctx) -> dict:
-    ms = (ctypes.c_double * 3)()
-    n = (ctypes.c_int64 * 3)()
+    """Summed device ms and launch counts per kind: keys ms_<kind>, n_<kind>."""
+    ms = (ctypes.c_double * HOM_PROFILE_KINDS)()
+    n = (ctypes.c_int64 * HOM_PROFILE_KINDS)()
     _check(lib().hom_profile_read(ctx, ms, n), ctx)
-    return dict(ms_transposing=ms[0], ms_in_place=ms[1], ms_transpose=ms[2],
-                n_transposing=n[0], n_in_place=n[1], n_transpose=n[2])
+    out = {}
+    for i, k in enumerate(PROFILE_KINDS):
+        out["ms_" + k] = ms[i]
+        out["n_" + k] = n[i]
+    return out
 
 
 def hom_autotune_info(ctx) -> dict:
     v = (ctypes.c_int32 * 3)()
-    ms = (ctypes.c_double * 6)()
+    ms = (ctypes.c_double * 7)()
     _check(lib().hom_autotune_info(ctx, v, ms), ctx)
     return dict(variants=list(v[:2]), strategy=v[2], pass_ms=list(ms[:4]), step_ms=list(ms[4:]))
 

@@ -18,7 +18,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhom.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-UNITS = ["hom_api.cu", "hom_kern_c64.cu", "hom_kern_c128.cu", "hom_static.cu"]
+UNITS = ["hom_api.cu", "hom_kern_c64.cu", "hom_kern_c64_rows.cu", "hom_kern_c128.cu", "hom_kern_c128_rows.cu",
+         "hom_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

@@ -28,6 +28,8 @@ using cd = std::complex<double>;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
 constexpr size_t kAlign = 256;
+constexpr int kKinds = HOM_PROFILE_KINDS;   // launch kinds timed by hom_profile
+constexpr int kStrategies = 3;              // step sequences (see step_sequence)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -190,8 +192,8 @@ struct hom_ctx {
   std::vector<cudaEvent_t> ev;     // event pool
   std::vector<int> ev_kind;        // per recorded pair: kind (see kNumKinds)
   size_t ev_used;
-  double prof_ms[3];               // transposing pass, in-place pass, transpose
-  long long prof_n[3];
+  double prof_ms[kKinds];          // transposing pass, in-place pass, transpose, double in-place pass
+  long long prof_n[kKinds];
   // CUDA graphs of the forward step sequence, one per step count
   bool use_graphs;
   // autotuner: kernel variant of the transposing [0] and in-place [1] passes,
@@ -201,8 +203,8 @@ struct hom_ctx {
   int strategy;
   bool tuned;
   bool tune_enabled;
-  double tune_ms[2][2];   // [pass kind][variant], device ms of a timed 2-step run
-  double tune_step_ms[2]; // [strategy], device ms of a timed 2-step run
+  double tune_ms[2][2];             // [transposing / in-place][variant], device ms per launch
+  double tune_step_ms[kStrategies]; // [strategy], estimated device ms per step
   // tensor maps of the buffers a transposing pass writes (state, transposed
   // buffer, adjoint state), per kernel variant; used where tma_store_width > 0
   CUtensorMap maps[3][2];
@@ -451,18 +453,24 @@ hom_status prof_end(hom_ctx* c, size_t idx, int kind) {
   return HOM_OK;
 }
 
-// One Strang step = two kinetic passes, one per particle (their sandwiches
-// commute, so either goes first).  The state lives in psi = psi[r1][r2]
-// (layout A) or, between steps, in the workspace buffer as psi[r2][r1]
-// (layout B).  The first pass of a step reads the rows of the layout that
-// holds the state (the planes of one particle) and writes them transposed
-// into the other layout, whose rows are the other particle's planes; the
-// second pass works in place there.  So the state alternates between the two
-// layouts from step to step, each step costs one transposed store, and an
-// even number of steps ends in layout A (an odd number ends with a second
-// transposing pass back to A).  The potential phase (dt/2 on the first step,
-// dt after: the halves of neighbouring steps fused) is applied on the first
-// load of every step, the closing dt/2 on the last store.
+// One Strang step applies one kinetic sandwich per particle; the two commute,
+// so either goes first.  The state lives in psi = psi[r1][r2] (layout A) or,
+// between steps, in the workspace buffer as psi[r2][r1] (layout B).  A
+// sandwich works on the rows of a layout (the planes of one particle), so the
+// other particle's sandwich needs the state transposed.  The potential phase
+// (dt/2 on the first step, dt between steps: the halves of neighbouring steps
+// fused) is applied on a load, the closing dt/2 on the last store.  Three
+// ways of sequencing the passes (c->strategy):
+//   0: a transposing pass (rows of one layout in, the other layout out), then
+//      an in-place pass there; the state alternates between the layouts and
+//      an odd count ends with a second transposing pass back to A;
+//   1: an in-place pass, a plain transpose, an in-place pass;
+//   2: steps overlap: after the first sandwich, each transpose is followed by
+//      one double in-place pass holding this step's second sandwich, the
+//      potential of the full step and the next step's first sandwich, all of
+//      the same particle (so two HBM round trips per step); the last step
+//      ends with a single in-place pass (and a transpose back to A if needed).
+// All three apply the same arithmetic to every element in the same order.
 template <typename T>
 hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   using C = typename hom::Cx<T>::type;
@@ -532,6 +540,45 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     if (c->prof && (st = prof_end(c, ev, 2)) != HOM_OK) return st;
     return HOM_OK;
   };
+  auto double_in_place = [&](C* buf) -> hom_status {
+    hom::PassArgs<C> a{};
+    a.psi = buf;
+    a.qa = qa;
+    a.qt = qt;
+    a.gy = gy;
+    a.twx = twx;
+    a.twy = twy;
+    a.p1 = p1h;
+    a.p12 = p12h;
+    a.p1m = p1f;
+    a.p12m = p12f;
+    a.v_load = 0;
+    a.v_store = 0;
+    size_t ev = 0;
+    hom_status st;
+    if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    HOM_CUDA(c, (hom::launch_kinetic2<T>(p.nx, p.ny, c->variant[1], a, p.batch, c->stream)));
+    if (c->prof && (st = prof_end(c, ev, 3)) != HOM_OK) return st;
+    return HOM_OK;
+  };
+  if (c->strategy == 2) {
+    hom_status st = in_place_v(A, 1, 0, p1h, p12h);
+    if (st != HOM_OK) return st;
+    for (int s = 0; s < nsteps; ++s) {
+      C* cur = in_a ? A : Bp;
+      C* oth = in_a ? Bp : A;
+      if ((st = transpose(cur, oth)) != HOM_OK) return st;
+      in_a = !in_a;
+      if (s < nsteps - 1) {
+        st = double_in_place(oth);
+      } else {
+        st = in_place_v(oth, 0, 1, p1h, p12h);
+        if (st == HOM_OK && !in_a) st = transpose(Bp, A);
+      }
+      if (st != HOM_OK) return st;
+    }
+    return HOM_OK;
+  }
   if (c->strategy == 1) {
     // in-place pass (potential phase at load), transpose, in-place pass
     for (int s = 0; s < nsteps; ++s) {
@@ -575,21 +622,24 @@ hom_status run_steps(hom_ctx* c, char* psi, int nsteps, int sgn) {
 }
 
 // Autotuner: the kernel variants of a pass (Geo, variant 0 or 1) differ only
-// in thread counts and cluster widths, and the two step strategies only in
-// where the transposition happens, so every element of the state sees the
-// same arithmetic and the results are bitwise identical.  The first forward
-// hom_step call with at least kTuneMinSteps steps runs, for each variant
-// under strategy 0 and then for the better variants under strategy 1, two
-// steps to warm up and two timed steps (CUDA events around every launch) on
-// the real state; the fastest choice is kept for the context.  Those 12 steps
-// are part of the requested steps.
+// in thread counts and cluster widths, and the step strategies only in where
+// the transposition happens, so every element of the state sees the same
+// arithmetic and the results are bitwise identical.  The first forward
+// hom_step call with at least kTuneMinSteps steps runs three trials on the
+// real state, each two steps to warm up and two timed steps (CUDA events
+// around every launch): strategy 0 with all passes in variant 0, the same in
+// variant 1, and strategy 2 with the faster variant of each pass.  From the
+// average launch times it estimates the steady-state step of each strategy
+// (0: transposing + in-place pass; 1: two in-place passes + transpose; 2:
+// double in-place pass + transpose) and keeps the fastest.  The 12 steps of
+// the trials are part of the requested steps.
 constexpr int kTuneMinSteps = 24;
 
 hom_status autotune(hom_ctx* c) {
   const bool prof_saved = c->prof;
-  double ms_saved[3];
-  long long n_saved[3];
-  for (int k = 0; k < 3; ++k) {
+  double ms_saved[kKinds];
+  long long n_saved[kKinds];
+  for (int k = 0; k < kKinds; ++k) {
     ms_saved[k] = c->prof_ms[k];
     n_saved[k] = c->prof_n[k];
   }
@@ -599,8 +649,8 @@ hom_status autotune(hom_ctx* c) {
     c->ev.resize(kEventPool, nullptr);
     for (auto& e : c->ev) HOM_CUDA(c, cudaEventCreate(&e));
   }
-  // two untimed then two timed steps of a configuration; returns the kinds' ms
-  auto trial = [&](int strategy, int v0, int v1, double* ms) -> hom_status {
+  // two untimed then two timed steps of a configuration; average ms per launch of each kind
+  auto trial = [&](int strategy, int v0, int v1, double* avg) -> hom_status {
     c->strategy = strategy;
     c->variant[0] = v0;
     c->variant[1] = v1;
@@ -608,31 +658,35 @@ hom_status autotune(hom_ctx* c) {
     hom_status st;
     if ((st = run_steps(c, c->state, 2, 0)) != HOM_OK) return st;
     c->prof = true;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
       c->prof_ms[k] = 0.0;
       c->prof_n[k] = 0;
     }
     if ((st = run_steps(c, c->state, 2, 0)) != HOM_OK) return st;
     if ((st = harvest_events(c)) != HOM_OK) return st;
-    for (int k = 0; k < 3; ++k) ms[k] = c->prof_ms[k];
+    for (int k = 0; k < kKinds; ++k) avg[k] = c->prof_n[k] > 0 ? c->prof_ms[k] / (double)c->prof_n[k] : 0.0;
     return HOM_OK;
   };
-  double ms[3];
+  double avg[kKinds];
   for (int v = 0; v < 2; ++v) {
-    if ((s = trial(0, v, v, ms)) != HOM_OK) return s;
-    c->tune_ms[0][v] = ms[0];
-    c->tune_ms[1][v] = ms[1];
+    if ((s = trial(0, v, v, avg)) != HOM_OK) return s;
+    c->tune_ms[0][v] = avg[0];
+    c->tune_ms[1][v] = avg[1];
   }
   const int v0 = c->tune_ms[0][1] < c->tune_ms[0][0] ? 1 : 0;
   const int v1 = c->tune_ms[1][1] < c->tune_ms[1][0] ? 1 : 0;
+  if ((s = trial(2, v0, v1, avg)) != HOM_OK) return s;
   c->tune_step_ms[0] = c->tune_ms[0][v0] + c->tune_ms[1][v1];
-  if ((s = trial(1, v0, v1, ms)) != HOM_OK) return s;
-  c->tune_step_ms[1] = ms[1] + ms[2];
-  c->strategy = c->tune_step_ms[1] < c->tune_step_ms[0] ? 1 : 0;
+  c->tune_step_ms[1] = 2.0 * c->tune_ms[1][v1] + avg[2];
+  c->tune_step_ms[2] = avg[3] + avg[2];
+  int best = 0;
+  for (int k = 1; k < kStrategies; ++k)
+    if (c->tune_step_ms[k] < c->tune_step_ms[best]) best = k;
+  c->strategy = best;
   c->variant[0] = v0;
   c->variant[1] = v1;
   c->prof = prof_saved;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kKinds; ++k) {
     c->prof_ms[k] = ms_saved[k];
     c->prof_n[k] = n_saved[k];
   }
@@ -780,7 +834,7 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
   c->err = "no error";
   c->prof = false;
   c->ev_used = 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kKinds; ++k) {
     c->prof_ms[k] = 0.0;
     c->prof_n[k] = 0;
   }
@@ -793,7 +847,7 @@ hom_status hom_create(const hom_params* p, void* d_state, void* d_workspace, siz
     c->strategy = 0;
     c->tuned = false;
     for (auto& r : c->tune_ms) r[0] = r[1] = 0.0;
-    c->tune_step_ms[0] = c->tune_step_ms[1] = 0.0;
+    for (auto& t : c->tune_step_ms) t = 0.0;
   }
   c->sims.assign(p->batch, SimParams{p->qpc_h, p->qpc_w, p->coul_lambda});
   c->have_packets.assign(p->batch, 0);
@@ -1057,8 +1111,9 @@ hom_status hom_autotune_set(hom_ctx* c, const int32_t* choice) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if (!choice) return fail(c, HOM_ERR_ARG, "choice is NULL");
-  for (int k = 0; k < 3; ++k)
-    if (choice[k] != 0 && choice[k] != 1) return fail(c, HOM_ERR_ARG, "autotune choices must be 0 or 1");
+  for (int k = 0; k < 2; ++k)
+    if (choice[k] != 0 && choice[k] != 1) return fail(c, HOM_ERR_ARG, "kernel variants must be 0 or 1");
+  if (choice[2] < 0 || choice[2] >= kStrategies) return fail(c, HOM_ERR_ARG, "strategy must be 0, 1 or 2");
   c->variant[0] = choice[0];
   c->variant[1] = choice[1];
   c->strategy = choice[2];
@@ -1078,8 +1133,7 @@ hom_status hom_autotune_info(hom_ctx* c, int32_t* choice, double* ms) {
   if (ms) {
     for (int k = 0; k < 2; ++k)
       for (int v = 0; v < 2; ++v) ms[2 * k + v] = c->tune_ms[k][v];
-    ms[4] = c->tune_step_ms[0];
-    ms[5] = c->tune_step_ms[1];
+    for (int k = 0; k < kStrategies; ++k) ms[4 + k] = c->tune_step_ms[k];
   }
   return HOM_OK;
 }
@@ -1095,7 +1149,7 @@ hom_status hom_profile(hom_ctx* c, int32_t enable) {
     HOM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->ev_used = 0;
     c->ev_kind.clear();
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
       c->prof_ms[k] = 0.0;
       c->prof_n[k] = 0;
     }
@@ -1108,7 +1162,7 @@ hom_status hom_profile_read(hom_ctx* c, double* ms, int64_t* counts) {
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if ((s = harvest_events(c)) != HOM_OK) return s;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kKinds; ++k) {
     if (ms) ms[k] = c->prof_ms[k];
     if (counts) counts[k] = c->prof_n[k];
   }

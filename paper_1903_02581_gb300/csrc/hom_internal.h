@@ -24,11 +24,19 @@ template <typename T> GeoInfo geo_info(int nx, int ny, bool col);
 // kinetic passes of a grid on the current device, so that later launches,
 // including launches captured into a CUDA graph, make no attribute calls.
 template <typename T> cudaError_t prepare_kinetic(int nx, int ny);
+// The same for the in-place passes only (called by prepare_kinetic).
+template <typename T> cudaError_t prepare_kinetic_rows(int nx, int ny);
 
 // In-place pass on rows (kinetic_pass), variant 0 or 1 (see Geo).
 template <typename T>
 cudaError_t launch_kinetic(int nx, int ny, int variant, const PassArgs<typename Cx<T>::type>& a, int batch,
                            cudaStream_t s);
+
+// Double in-place pass: two sandwiches with the potential phase a.p1m/a.p12m
+// between them (see kinetic_pass), variant 0 or 1.
+template <typename T>
+cudaError_t launch_kinetic2(int nx, int ny, int variant, const PassArgs<typename Cx<T>::type>& a, int batch,
+                            cudaStream_t s);
 
 // Transposing pass (kinetic_pass_t), variant 0 or 1.
 template <typename T>

@@ -1,6 +1,8 @@
-// Kernels of libhom in complex64 (FP32 arithmetic, FP64 reductions).
+// Kernels of libhom in complex64 (FP32 arithmetic, FP64 reductions): the
+// transposing pass and every kernel but the in-place passes.
 #define HOM_T float
 #define HOM_WIDE 1
+#define HOM_PART 2
 #include "hom_kern.inc"
 
 namespace hom {

@@ -43,6 +43,8 @@ template <typename C> struct PassArgs {
   const C* twy;        // e^{-2 pi i j / ny}, j < ny: hi parts, then lo parts
   const C* p1;         // e^{-i tau V1(r)} - 1                 [batch][n]   (tau = dt/2 or dt)
   const C* p12;        // e^{-i tau V12(dx, dy)} - 1           [batch][(2nx-1)(2ny-1)]
+  const C* p1m;        // double pass: the potential between its two sandwiches (tau = dt)
+  const C* p12m;
   int v_load;          // apply the potential phase when loading
   int v_store;         // apply the potential phase when storing
   int pref_ahead;      // prefetch into L2 the tile this many CTAs ahead (0: off)
@@ -456,6 +458,46 @@ __device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__
   }
 }
 
+// Between the two sandwiches of a double pass, in registers: the last inverse
+// x stage of a line (m, y) yields the x positions m + N2*m2, which are exactly
+// the inputs N2*n1 + n2 (n2 = m) of a first forward x stage, so the thread
+// inverts, applies the potential phase of the full step (the same call, with
+// the plane index first, as a pass that applies it on load), transforms
+// forward again and writes back the shared-memory positions it read.  With
+// nx <= 16 this is the whole inverse and forward x transform, followed by the
+// T_x/2 hook.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, class Hook>
+__device__ __forceinline__ void x_turnaround(C* sm, const C* tw, int t0, const C* __restrict__ p1,
+                                             const C* __restrict__ p12, Hook& hook) {
+  using S = Split<NX>;
+  constexpr int N1 = S::N1, N2 = S::N2;
+  for (int it = threadIdx.x; it < G * NY * N2; it += NT) {
+    int g, y, m;
+    decode_item<false, NY, G, N2>(it, g, y, m);
+    C* line = sm + g * PS + y;
+    C v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[(N2 * k1 + m) * RS];
+    dft_reg<N1, true>(v);
+    C d[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) d[n1] = vphase_delta<C, NX, NY>(p1, p12, t0 + g, (N2 * n1 + m) * NY + y);
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = apply_delta(v[n1], d[n1]);
+    dft_reg<N1, false>(v);
+    if constexpr (N2 == 1) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
+    } else {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[m * k1], tw[NX + m * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + m) * RS] = v[k1];
+    }
+  }
+  __syncthreads();
+}
+
 // Transposed store of a cluster of CL CTAs holding W = CL*G adjacent planes:
 // CTA q gathers, for every plane, the inputs of the last inverse x stage of
 // the lines m1 = q (mod CL) from the owning CTA (distributed shared memory),
@@ -489,7 +531,10 @@ __device__ __forceinline__ void x_inverse_cluster_store(const C* sm, C* __restri
 
 // In-place pass: one kinetic sandwich on G contiguous rows of psi (the plane
 // of one particle for a fixed coordinate of the other), written back in place.
-template <typename T, int NX, int NY, int V>
+// TWICE: two sandwiches of the same particle with the potential phase of a
+// full step between them (the end of one Strang step and the start of the
+// next, when the state is not transposed in between).
+template <typename T, int NX, int NY, int V, bool TWICE>
 __global__ void __launch_bounds__(Geo<T, NX, NY, false, V>::NT)
 kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   using Gm = Geo<T, NX, NY, false, V>;
@@ -523,6 +568,13 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
   y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
   if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+  if constexpr (TWICE) {
+    x_turnaround<C, NX, NY, G, NT, RS, PS>(sm, stwx, t0, a.p1m + (size_t)b * N,
+                                           a.p12m + (size_t)b * (2 * NX - 1) * (2 * NY - 1), qa);
+    if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
+    y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
+    if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+  }
   x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false>(sm, base, t0, p1, p12, a.v_store != 0);
 }
 

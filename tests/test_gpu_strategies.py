@@ -1,8 +1,10 @@
 """Step strategies and kernel variants of libhom give bitwise-identical states.
 
 Strategy 0 runs a transposing pass and an in-place pass per Strang step,
-strategy 1 an in-place pass, a plain transpose and an in-place pass; each
-kinetic pass has two launch variants.  All of them apply the same arithmetic
+strategy 1 an in-place pass, a plain transpose and an in-place pass, and
+strategy 2 a transpose and a double in-place pass (the end of one step, the
+potential between steps and the start of the next); each kinetic pass has
+two launch variants.  All of them apply the same arithmetic
 to every element, so the states after any number of steps must agree bit for
 bit, and one of them is checked against the FP64 oracle.
 """
@@ -45,12 +47,12 @@ def small_w(nx, ny, prec):
     return w
 
 
-CHOICES = list(itertools.product((0, 1), (0, 1), (0, 1)))
+CHOICES = list(itertools.product((0, 1), (0, 1), (0, 1, 2)))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 16), (64, 32), (128, 16)])
-@pytest.mark.parametrize("nsteps", [1, 4, 5])
+@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 16), (64, 32), (128, 16), (16, 64)])
+@pytest.mark.parametrize("nsteps", [1, 2, 5])
 def test_choices_bitwise_identical(prec, nx, ny, nsteps):
     w = small_w(nx, ny, prec)
     psi = W.random_state((nx, ny, nx, ny), seed=nx + 7 * ny + nsteps)
@@ -92,12 +94,33 @@ def test_strategy_one_batched_profile_counts():
     H().hom_profile(pr.ctx, 0)
 
 
+def test_strategy_two_profile_counts():
+    w = small_w(32, 16, "c64")
+    pr = H().Propagator(w)
+    H().hom_autotune_set(pr.ctx, 1, 1, 2)
+    H().hom_profile(pr.ctx, 1)
+    pr.step(3)
+    prof = H().hom_profile_read(pr.ctx)
+    # in-place (opening phase); then per step a transpose and a double pass,
+    # the last step a single in-place pass and (odd count) a transpose back
+    assert prof["n_in_place"] == 2
+    assert prof["n_double"] == 2
+    assert prof["n_transpose"] == 4
+    assert prof["n_transposing"] == 0
+    pr.step(4)
+    prof = H().hom_profile_read(pr.ctx)
+    assert (prof["n_in_place"], prof["n_double"], prof["n_transpose"]) == (4, 5, 8)
+    H().hom_profile(pr.ctx, 0)
+
+
 def test_autotune_set_rejects_bad_choice():
     w = small_w(16, 16, "c64")
     pr = H().Propagator(w)
     with pytest.raises(H().HomError) as e:
         H().hom_autotune_set(pr.ctx, 0, 2, 0)
     assert e.value.status == H().HOM_ERR_ARG
+    with pytest.raises(H().HomError):
+        H().hom_autotune_set(pr.ctx, 0, 0, 3)
 
 
 def test_autotune_reports_both_strategies():
@@ -106,9 +129,10 @@ def test_autotune_reports_both_strategies():
     before = pr.get_state(0)
     pr.step(24)
     info = H().hom_autotune_info(pr.ctx)
-    assert info["strategy"] in (0, 1)
+    assert info["strategy"] in (0, 1, 2)
     assert all(v in (0, 1) for v in info["variants"])
-    assert info["step_ms"][0] > 0.0 and info["step_ms"][1] > 0.0
+    assert len(info["step_ms"]) == 3 and min(info["step_ms"]) > 0.0
+    assert info["step_ms"][info["strategy"]] == min(info["step_ms"])
     # the tuner's 12 steps (six calls of 2) are part of the 24
     ref = H().Propagator(w)
     H().hom_autotune_set(ref.ctx, 0, 0, 0)
