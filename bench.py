@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--pin", default=None,
+                    help="fix the kernel choice instead of autotuning: 'transposing variant,in-place variant,strategy'")
     return ap.parse_args()
 
 
@@ -333,6 +335,8 @@ def gb300_arm(args):
     pts = (w["nx"] * w["ny"]) ** 2
     batch = len(w["sims"])
     pr = H.Propagator(w, device=f"cuda:{local}")
+    if args.pin:
+        H.hom_autotune_set(pr.ctx, *[int(v) for v in args.pin.split(",")])
     stream = pr.stream
 
     def bench_step():

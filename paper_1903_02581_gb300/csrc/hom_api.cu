@@ -294,14 +294,14 @@ hom_status build_shared_tables(hom_ctx* c) {
     if ((s = upload(c, c->L.gy[sgn], gy.data(), gy.size())) != HOM_OK) return s;
     HOM_CUDA(c, cudaStreamSynchronize(c->stream));
   }
-  // twiddles e^{-2 pi i j / n} as hi parts then lo parts (lo = 0 in FP64)
+  // twiddles e^{-2 pi i j / n} as interleaved (hi, lo) pairs (lo = 0 in FP64)
   auto twiddles = [&](std::vector<unsigned char>& buf, int nn) {
     for (int j = 0; j < nn; ++j) {
       const double a = kTwoPi * j / nn;
       const cd w(std::cos(a), -std::sin(a));
       const cd hi = dbl ? w : cd((float)w.real(), (float)w.imag());
-      put(buf, dbl, j, hi);
-      put(buf, dbl, nn + j, dbl ? cd(0, 0) : w - hi);
+      put(buf, dbl, 2 * j, hi);
+      put(buf, dbl, 2 * j + 1, dbl ? cd(0, 0) : w - hi);
     }
   };
   twiddles(twx, nx);

@@ -87,6 +87,18 @@ __device__ __forceinline__ C cmul_hl(C v, C hi, C lo) {
   }
 }
 
+// v * W_j (or its conjugate) from a twiddle table stored as interleaved
+// (hi, lo) pairs: in FP32 the pair is one 16-byte load.
+template <bool CONJ, typename C>
+__device__ __forceinline__ C cmul_tw(C v, const C* tw, int j) {
+  if constexpr (sizeof(C) == 8) {
+    const float4 t = *reinterpret_cast<const float4*>(tw + 2 * j);
+    return cmul_hl<CONJ>(v, C{t.x, t.y}, C{t.z, t.w});
+  } else {
+    return cmul_hl<CONJ>(v, tw[2 * j], tw[2 * j + 1]);
+  }
+}
+
 template <typename R> __device__ __forceinline__ R hi_part(double v) { return (R)v; }
 template <typename R> __device__ __forceinline__ R lo_part(double v) {
   return sizeof(R) == 8 ? (R)0 : (R)(v - (double)(float)v);

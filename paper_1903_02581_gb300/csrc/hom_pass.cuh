@@ -39,8 +39,8 @@ template <typename C> struct PassArgs {
   const C* qa;         // e^{-i dt/4 (k_x - B y)^2} - 1        [x position][y]
   const C* qt;         // the same table transposed            [y][x position]
   const C* gy;         // e^{-i dt/2 k_y^2} - 1                [y position]
-  const C* twx;        // e^{-2 pi i j / nx}, j < nx: hi parts, then lo parts
-  const C* twy;        // e^{-2 pi i j / ny}, j < ny: hi parts, then lo parts
+  const C* twx;        // e^{-2 pi i j / nx}, j < nx: interleaved (hi, lo) pairs
+  const C* twy;        // e^{-2 pi i j / ny}, j < ny: interleaved (hi, lo) pairs
   const C* p1;         // e^{-i tau V1(r)} - 1                 [batch][n]   (tau = dt/2 or dt)
   const C* p12;        // e^{-i tau V12(dx, dy)} - 1           [batch][(2nx-1)(2ny-1)]
   const C* p1m;        // double pass: the potential between its two sandwiches (tau = dt)
@@ -101,7 +101,9 @@ template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   static constexpr int PSM = (G >= LW) ? 1 : (LW / G);
   static constexpr int PS = PS0 + ((((PSM - PS0) % LW) + LW) % LW);
   static constexpr int ELEMS = G * PS;
-  static constexpr size_t SMEM = (size_t)(ELEMS + 2 * NX + 2 * NY) * sizeof(C);
+  // twiddle tables after the planes, 16-byte aligned (one (hi, lo) pair per load)
+  static constexpr int TWOFF = (ELEMS + 1) / 2 * 2;
+  static constexpr size_t SMEM = (size_t)(TWOFF + 2 * NX + 2 * NY) * sizeof(C);
   static constexpr int TILES_PER_SIM = N / G;
   static_assert(N % G == 0, "tile");
   // Transposing pass with fewer than 4 planes per CTA: a cluster of CL CTAs
@@ -121,7 +123,7 @@ template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   // columns (see x_inverse_cluster_store_tma)
   static constexpr bool TMA_STORE = COL && CL > 1 && sizeof(C) == 8;
   static constexpr int STAGE = TMA_STORE ? 2 * Split<NX>::N1 * NY * CL * G : 0;
-  static constexpr size_t STAGE_OFF = ((size_t)(ELEMS + 2 * NX + 2 * NY) * sizeof(C) + 127) / 128 * 128;
+  static constexpr size_t STAGE_OFF = (SMEM + 127) / 128 * 128;
   // + 128 bytes of slack: the kernel rounds the staging address up to 128 bytes
   static constexpr size_t SMEM_ALL = TMA_STORE ? STAGE_OFF + (size_t)STAGE * sizeof(C) + 128 : SMEM;
 };
@@ -163,7 +165,7 @@ __device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = line[(N2 * n1 + n2) * RS];
       dft_reg<N1, false>(v);
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NX + n2 * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + n2) * RS] = v[k1];
     }
@@ -218,7 +220,7 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = row[N2 * n1 + n2];
       dft_reg<N1, false>(v);
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NY + n2 * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1 + n2] = v[k1];
     }
@@ -234,7 +236,7 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
       for (int k2 = 0; k2 < N2; ++k2) v[k2] = apply_delta(v[k2], ldg(gy + N2 * k1 + k2));
       dft_reg<N2, true>(v);
 #pragma unroll
-      for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_hl<true>(v[m1], tw[m1 * k1], tw[NY + m1 * k1]);
+      for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_tw<true>(v[m1], tw, m1 * k1);
 #pragma unroll
       for (int m1 = 0; m1 < N2; ++m1) row[N2 * k1 + m1] = v[m1];
     }
@@ -283,7 +285,7 @@ __device__ __forceinline__ void y_forward(C* sm, const C* tw, Hook& hook) {
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = row[N2 * n1 + n2];
       dft_reg<N1, false>(v);
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NY + n2 * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1 + n2] = v[k1];
     }
@@ -352,7 +354,8 @@ __device__ __forceinline__ size_t global_offset(int t0, int g, int x, int y) {
   else return (size_t)(x * NY + y) * N + (t0 + g);
 }
 
-// First x stage read straight from global memory: every thread loads the N1
+// First x stage read straight from global memory (streaming loads: the state
+// is read once per pass): every thread loads the N1
 // elements of its line segment (all in flight at once), applies the potential
 // phase if asked (it is symmetric in the two particles, so the plane index
 // t0 + g and the element index may be either particle's), transforms, and
@@ -369,7 +372,7 @@ __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const 
     decode_item<COL, NY, G, N2>(it, g, y, n2);
     C v[N1];
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) v[n1] = base[global_offset<COL, NX, NY>(t0, g, N2 * n1 + n2, y)];
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = __ldcs(base + global_offset<COL, NX, NY>(t0, g, N2 * n1 + n2, y));
     if (apply_v) {
       C d[N1];
 #pragma unroll
@@ -384,7 +387,7 @@ __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const 
       for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
     } else {
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[n2 * k1], tw[NX + n2 * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + n2) * RS] = v[k1];
     }
@@ -423,15 +426,16 @@ __device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
     for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[(N2 * k1 + k2) * RS];
     dft_reg<N2, true>(v);
 #pragma unroll
-    for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_hl<true>(v[m1], tw[m1 * k1], tw[NX + m1 * k1]);
+    for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_tw<true>(v[m1], tw, m1 * k1);
 #pragma unroll
     for (int m1 = 0; m1 < N2; ++m1) line[(N2 * k1 + m1) * RS] = v[m1];
   }
   __syncthreads();
 }
 
-// Last inverse x stage written straight to global memory (the whole inverse
-// x transform when nx <= 16), with the closing potential phase if asked.
+// Last inverse x stage written straight to global memory with streaming
+// stores (the whole inverse x transform when nx <= 16), with the closing
+// potential phase if asked.
 // COL = false writes the planes back as rows; COL = true writes them
 // transposed (element (x, y) of plane t0 + g to row x*ny + y, column t0 + g).
 template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL>
@@ -454,7 +458,7 @@ __device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__
         v[m2] = apply_delta(v[m2], vphase_delta<C, NX, NY>(p1, p12, (m1 + N2 * m2) * NY + y, t0 + g));
     }
 #pragma unroll
-    for (int m2 = 0; m2 < N1; ++m2) base[global_offset<COL, NX, NY>(t0, g, m1 + N2 * m2, y)] = v[m2];
+    for (int m2 = 0; m2 < N1; ++m2) __stcs(base + global_offset<COL, NX, NY>(t0, g, m1 + N2 * m2, y), v[m2]);
   }
 }
 
@@ -490,7 +494,7 @@ __device__ __forceinline__ void x_turnaround(C* sm, const C* tw, int t0, const C
       for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
     } else {
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_hl<false>(v[k1], tw[m * k1], tw[NX + m * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, m * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + m) * RS] = v[k1];
     }
@@ -543,7 +547,7 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   constexpr int N2X = Split<NX>::N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  C* stwx = sm + Gm::ELEMS;
+  C* stwx = sm + Gm::TWOFF;
   C* stwy = stwx + 2 * NX;
   const int tid = threadIdx.x;
   for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
@@ -656,7 +660,7 @@ kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
   constexpr int N2X = Split<NX>::N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  C* stwx = sm + Gm::ELEMS;
+  C* stwx = sm + Gm::TWOFF;
   C* stwy = stwx + 2 * NX;
   const int tid = threadIdx.x;
   for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
@@ -706,8 +710,9 @@ kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
 
 // dst[b][c][r] = src[b][r][c] for a batch of [n][n] states: tiles of T x T
 // through shared memory (row stride T + 1: conflict-free column reads), rows
-// read and written as contiguous T-element segments.  Used between two
-// in-place passes by the second step strategy (see step_sequence).
+// read and written as contiguous T-element segments, both with streaming
+// (evict-first) cache hints: every byte is touched once.  Used between
+// in-place passes by step strategies 1 and 2 (see step_sequence).
 template <typename C, int T>
 __global__ void __launch_bounds__(256) transpose_state(const C* __restrict__ src, C* __restrict__ dst, int n,
                                                        int batch) {
@@ -720,13 +725,13 @@ __global__ void __launch_bounds__(256) transpose_state(const C* __restrict__ src
     C* d = dst + (size_t)b * n * n;
     C v[T / ROWS];
 #pragma unroll
-    for (int i = 0; i < T / ROWS; ++i) v[i] = s[(size_t)(r0 + ty + i * ROWS) * n + c0 + tx];
+    for (int i = 0; i < T / ROWS; ++i) v[i] = __ldcs(s + (size_t)(r0 + ty + i * ROWS) * n + c0 + tx);
     if (b != (int)blockIdx.z) __syncthreads();        // previous simulation's tile fully read
 #pragma unroll
     for (int i = 0; i < T / ROWS; ++i) tile[ty + i * ROWS][tx] = v[i];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < T / ROWS; ++i) d[(size_t)(c0 + ty + i * ROWS) * n + r0 + tx] = tile[tx][ty + i * ROWS];
+    for (int i = 0; i < T / ROWS; ++i) __stcs(d + (size_t)(c0 + ty + i * ROWS) * n + r0 + tx, tile[tx][ty + i * ROWS]);
   }
 }
 
@@ -766,7 +771,7 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
   constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  C* stwx = sm + Gm::ELEMS;
+  C* stwx = sm + Gm::TWOFF;
   C* stwy = stwx + 2 * NX;
   __shared__ double red[32];
   const int tid = threadIdx.x;
