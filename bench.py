@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--workload", default="fullscale", choices=["fullscale", "batched"],
+                    help="fullscale: one 256x64 simulation (the headline); batched: 32 simulations of 128x32")
     ap.add_argument("--pin", default=None,
                     help="fix the kernel choice instead of autotuning: 'transposing variant,in-place variant,strategy'")
     return ap.parse_args()
@@ -208,7 +210,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample_rate(steps: int = 1):
+def oracle_sample_rate(steps: int = 1, workload: str = "fullscale"):
     """FP64 oracle on the bounded sample; returns (updates/s, seconds, description)."""
     import numpy as np
 
@@ -216,6 +218,21 @@ def oracle_sample_rate(steps: int = 1):
     from oracle import hom_oracle as O
     from paper_1903_02581_gb300 import workloads as W
 
+    if workload == "batched":
+        w = W.batched()
+        sim = w["sims"][0]
+        w["sims"] = [sim]
+        m = A.model_for(w, sim)
+        psi = A.initial_state(w, sim)
+        V = O.v_total(m)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            psi = O.strang_step(psi, m, vtot=V)
+        sec = time.perf_counter() - t0
+        pts = (w["nx"] * w["ny"]) ** 2
+        assert np.isfinite(psi).all()
+        return pts * steps / sec, sec, (f"oracle Strang step(s) on simulation 0 of the batched workload "
+                                        f"(128x32 per electron, {pts:,} points, FP64, numpy), {steps} step(s)")
     w = W.fullscale(sigma=2.0)
     w = W.shrink(w, ny=SAMPLE_NY)
     w["dy"] = 0.25
@@ -330,8 +347,13 @@ def gb300_arm(args):
         dist.barrier()
     H.lib()
 
-    sigma = [2.0, 1.0, 4.0][rank % 3]
-    w = W.fullscale(sigma=sigma)
+    if args.workload == "batched":
+        w = W.batched()
+        wname = "batched-32x128x32"
+    else:
+        sigma = [2.0, 1.0, 4.0][rank % 3]
+        w = W.fullscale(sigma=sigma)
+        wname = "fullscale-256x64"
     pts = (w["nx"] * w["ny"]) ** 2
     batch = len(w["sims"])
     pr = H.Propagator(w, device=f"cuda:{local}")
@@ -404,7 +426,8 @@ def gb300_arm(args):
         roofline = {"bound": "hbm", "achieved": dom["hbm_gbs"], "peak": peak, "unit": "GB/s",
                     "frac": dom["hbm_frac"], "peak_source": peak_kind}
     step_ms = sum(k[1] for k in kinds) / max(args.steps * args.inner, 1)
-    roofline.update({"traffic": ncu_traffic(name), "kernel": name, "kernels": per_kernel,
+    roofline.update({"traffic": ncu_traffic(name) if args.workload == "fullscale" else None,
+                     "kernel": name, "kernels": per_kernel,
                      "hbm_peak_gbs": peak,
                      # the two-round-trip floor: 32 B per point per step (complex64)
                      "step_algorithmic_hbm_frac": 2 * algo_bytes / (step_ms / 1000.0) / 1e9 / peak,
@@ -413,16 +436,18 @@ def gb300_arm(args):
     # end to end through the C ABI: host state in pinned memory copied in every step
     e2e = None
     if not args.no_e2e:
-        host = torch.empty((pts,), dtype=torch.complex64, pin_memory=True)
+        host = torch.empty((batch, pts), dtype=torch.complex64, pin_memory=True)
         hview = host.numpy()
-        H.hom_copy_state(pr.ctx, 0, hview, to_device=False)
+        for b in range(batch):
+            H.hom_copy_state(pr.ctx, b, hview[b], to_device=False)
         nrep = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(nrep):
-            H.hom_copy_state(pr.ctx, 0, hview, to_device=True)
+            for b in range(batch):
+                H.hom_copy_state(pr.ctx, b, hview[b], to_device=True)
             pr.step(args.inner)
             pr.observables()
         torch.cuda.synchronize()
@@ -435,7 +460,7 @@ def gb300_arm(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sec, desc = oracle_sample_rate(1)
+        rate, sec, desc = oracle_sample_rate(1, args.workload)
         cpu = {"value": rate, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
                "seconds": sec}
 
@@ -450,10 +475,10 @@ def gb300_arm(args):
             "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "fullscale-256x64", "nx": w["nx"], "ny": w["ny"], "points_per_sim": pts,
+            "config": {"workload": wname, "nx": w["nx"], "ny": w["ny"], "points_per_sim": pts,
                        "sims_per_gpu": batch, "state": "complex64", "strang_steps_per_step": args.inner,
                        "observables_per_step": 1, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (2 GiB state), no flush"},
+                       "l2": f"inputs larger than L2 ({batch * pts * 8 / 2**30:.0f} GiB state), no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "precision": precision, "p_bunch_last": obs[0]["p_bunch"] if obs else None,
             "norm_last": obs[0]["norm"] if obs else None,
