@@ -23,6 +23,11 @@ What is followed, by passage
   of edge eigenstates e^{ik x} phi_k(y) of the confined Landau problem.
 * Eq. (p_bunching): bunching probability = probability that both particles
   are found on the same side of the beam splitter.
+* Captions of Fig. 2 and Fig. 3(b): conditional probability
+  |psi(x1,y1,x2*,y2*)|^2 and unconditional probability of particle 1,
+  P(x1,y1) = integral over (x2,y2) of |psi|^2.
+* Sec. V, Eq. (reduced_density) and the entropy below it: von Neumann entropy
+  of a 1D slice of the two-particle state (reading R9).
 
 Readings of the paper used here (silent, garbled or inconsistent passages)
 --------------------------------------------------------------------------
@@ -53,6 +58,12 @@ R6  Edge packet (Eq. singlepwp with the closed-form lowest hybrid level of the
     wavenumbers; k0 from E(k0) = energy, sign from the direction.
 R7  The combined two-particle state is renormalised numerically (the 1/sqrt2
     of Eq. twopstate assumes orthogonal packets).
+R9  Spatial entanglement (Sec. V): the 1D slice phi(x1,x2) = psi(x1, y1*, x2, y2*)
+    with x1 in a region T and x2 in a region B is renormalised (discrete sum of
+    |phi|^2 = 1); rho_T(x1,x1') = sum_{x2 in B} phi(x1,x2) conj(phi(x1',x2)) (the
+    printed phi*(x2,x1') of Eq. reduced_density is read as phi*(x1',x2), the
+    only form that is a density matrix); S = -Tr rho_T ln rho_T (the printed
+    formula lacks the minus sign; S >= 0 is the von Neumann entropy).
 R8  Adjoint: the Strang product is palindromic and each factor unitary, so
     S(dt)^dagger = S(-dt); the gradient of L = <psi_N|M|psi_N> with respect
     to a potential parameter theta is
@@ -65,7 +76,9 @@ forms and invariants (DFT vs numpy.fft, unitarity, exchange symmetry,
 factorisation at zero Coulomb, free Gaussian spreading, Landau / hybrid level
 phases, cyclotron motion, Strang/Lie convergence orders, time reversal,
 energy conservation, Coulomb expectation by quadrature, packet energy,
-adjoint dot-product test and finite differences).
+adjoint dot-product test and finite differences, marginals and conditional
+slices of product and Slater states in closed form, entropies of states with
+known Schmidt coefficients).
 """
 
 from __future__ import annotations
@@ -424,3 +437,37 @@ def slater_dstate(alpha: np.ndarray, beta: np.ndarray, dbeta: np.ndarray,
     c = 1.0 / math.sqrt(nn)
     dc = -0.5 * c * dnn / nn
     return dc * u + c * du
+
+
+# ----------------------------------------------------------------------------
+# Observables beyond P_b: maps and entanglement (Fig. 2, Fig. 3(b), Sec. V)
+# ----------------------------------------------------------------------------
+
+def marginal(psi: np.ndarray, m: Model) -> np.ndarray:
+    """Unconditional probability density of particle 1, P(x1, y1) = sum over
+    (x2, y2) of |psi|^2 dx dy (caption of Fig. 3(b)); integrates to the norm."""
+    return np.sum(np.abs(psi) ** 2, axis=(AXIS_X2, AXIS_Y2)) * m.dx * m.dy
+
+
+def conditional(psi: np.ndarray, ix2: int, iy2: int) -> np.ndarray:
+    """Conditional probability |psi(x1, y1, x2*, y2*)|^2 at the grid point
+    (ix2, iy2) of particle 2 (caption of Fig. 2), unnormalised."""
+    return np.abs(psi[:, :, ix2, iy2]) ** 2
+
+
+def entanglement_entropy(psi: np.ndarray, iy1: int, iy2: int,
+                         x1_range: tuple[int, int], x2_range: tuple[int, int]) -> tuple[float, float]:
+    """Von Neumann entropy of the slice phi(x1, x2) = psi(x1, y1*, x2, y2*),
+    x1 in the index range x1_range (region T), x2 in x2_range (region B), as
+    in Sec. V with reading R9.  Returns (S, sum |phi|^2 before renormalising).
+    The eigenvalues of the Hermitian rho_T come from numpy.linalg.eigvalsh;
+    rounding leaves some at -1e-17, which count as 0 (0 ln 0 = 0)."""
+    a0, a1 = x1_range
+    b0, b1 = x2_range
+    phi = psi[a0:a1, iy1, b0:b1, iy2]
+    weight = float(np.sum(np.abs(phi) ** 2))
+    phi = phi / math.sqrt(weight)
+    rho = phi @ np.conj(phi).T                       # rho_T(x1, x1') = sum_x2 phi(x1,x2) phi*(x1',x2)
+    lam = np.linalg.eigvalsh(rho)
+    lam = lam[lam > 0.0]
+    return float(-np.sum(lam * np.log(lam))), weight

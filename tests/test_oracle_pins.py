@@ -369,3 +369,72 @@ def test_adjoint_gradient_matches_finite_differences():
     assert abs(loss - L(m, psi0)) < 1e-14
     for k, v in fd.items():
         assert abs(grad[k] - v) <= 1e-6 * max(abs(v), 1e-3), (k, grad[k], v)
+
+
+# --- observables beyond P_b: maps and entanglement (Fig. 2, Fig. 3(b), Sec. V) --
+
+def _orthonormal_pair(m, seed):
+    """Two single-particle functions on the grid, orthonormal in sum(conj(a) b) dx dy."""
+    a = W.random_state((m.nx, m.ny), seed=seed)
+    b = W.random_state((m.nx, m.ny), seed=seed + 1)
+    d1 = m.dx * m.dy
+    a = a / math.sqrt(np.sum(np.abs(a) ** 2) * d1)
+    b = b - a * (np.sum(np.conj(a) * b) * d1)
+    b = b / math.sqrt(np.sum(np.abs(b) ** 2) * d1)
+    return a, b
+
+
+def test_marginal_and_conditional_closed_forms():
+    m = small(nx=16, ny=8)
+    a, b = _orthonormal_pair(m, 11)
+    prod = np.einsum("ab,cd->abcd", a, b)
+    # product state: particle 1 is a, particle 2 is b
+    assert np.max(np.abs(O.marginal(prod, m) - np.abs(a) ** 2)) <= 1e-12 * np.max(np.abs(a) ** 2)
+    cond = O.conditional(prod, 3, 5)
+    assert np.max(np.abs(cond - np.abs(a) ** 2 * abs(b[3, 5]) ** 2)) <= 1e-12 * np.max(cond)
+    # Slater determinant of orthonormal a, b: each particle sees (|a|^2 + |b|^2)/2
+    sl = (prod - np.einsum("ab,cd->abcd", b, a)) / math.sqrt(2.0)
+    mg = O.marginal(sl, m)
+    assert np.max(np.abs(mg - 0.5 * (np.abs(a) ** 2 + np.abs(b) ** 2))) <= 1e-12 * np.max(mg)
+    assert abs(np.sum(mg) * m.dx * m.dy - 1.0) <= 1e-12
+    # Pauli: the conditional probability vanishes where particle 1 sits on particle 2
+    assert O.conditional(sl, 4, 6)[4, 6] <= 1e-30
+
+
+def _slice_state(m, iy1, iy2, x1r, x2r, probs, scale, seed):
+    """A 4D array whose slice (x1 in x1r, y1*, x2 in x2r, y2*) is
+    scale * sum_k sqrt(p_k) u_k(x1) v_k(x2) with orthonormal u_k, v_k, and
+    whose every other entry is unrelated noise."""
+    rng = np.random.default_rng(seed)
+    psi = W.random_state((m.nx, m.ny, m.nx, m.ny), seed=seed)
+    n1, n2 = x1r[1] - x1r[0], x2r[1] - x2r[0]
+    u, _ = np.linalg.qr(rng.standard_normal((n1, n1)) + 1j * rng.standard_normal((n1, n1)))
+    v, _ = np.linalg.qr(rng.standard_normal((n2, n2)) + 1j * rng.standard_normal((n2, n2)))
+    phi = sum(math.sqrt(p) * np.outer(u[:, k], v[:, k]) for k, p in enumerate(probs))
+    psi[x1r[0]:x1r[1], iy1, x2r[0]:x2r[1], iy2] = scale * phi
+    return psi
+
+
+@pytest.mark.parametrize("probs", [(1.0,), (0.5, 0.5), (0.5, 0.3, 0.2), (0.4, 0.3, 0.2, 0.1)])
+def test_entropy_of_known_schmidt_spectra(probs):
+    m = small(nx=16, ny=8)
+    x1r, x2r = (2, 9), (6, 16)                        # T and B of different sizes
+    psi = _slice_state(m, 2, 5, x1r, x2r, probs, scale=0.37, seed=21)
+    s, weight = O.entanglement_entropy(psi, 2, 5, x1r, x2r)
+    exact = -sum(p * math.log(p) for p in probs)
+    assert abs(s - exact) <= 1e-12
+    assert abs(weight - 0.37 ** 2) <= 1e-14
+    # the same state read on other y rows has a different (generic) entropy
+    s_other, _ = O.entanglement_entropy(psi, 3, 5, x1r, x2r)
+    assert abs(s_other - exact) > 1e-3
+
+
+def test_entropy_of_slater_slice_is_ln2():
+    m = small(nx=16, ny=8)
+    rng = np.random.default_rng(5)
+    q, _ = np.linalg.qr(rng.standard_normal((m.nx, 2)) + 1j * rng.standard_normal((m.nx, 2)))
+    u, v = q[:, 0], q[:, 1]
+    psi = np.zeros((m.nx, m.ny, m.nx, m.ny), dtype=np.complex128)
+    psi[:, 1, :, 1] = (np.outer(u, v) - np.outer(v, u)) / math.sqrt(2.0)
+    s, _ = O.entanglement_entropy(psi, 1, 1, (0, m.nx), (0, m.nx))
+    assert abs(s - math.log(2.0)) <= 1e-12
