@@ -197,6 +197,37 @@ hom_status hom_autotune_info(hom_ctx* ctx, int32_t* choice, double* ms);
  * hom_step calls use it and never tune.  Results do not depend on it. */
 hom_status hom_autotune_set(hom_ctx* ctx, const int32_t* choice);
 
+/* Probability maps and slices of the state (host outputs, FP64; each call
+ * synchronises the stream and uses the workspace's second state buffer as
+ * scratch, so it must not overlap a hom_step on another stream).
+ *
+ * hom_marginal: unconditional probability density of particle 1 (caption of
+ * Fig. 3(b)): out[b][x][y] = sum over (x2, y2) of |psi(x, y, x2, y2)|^2 dx dy
+ * for every simulation (batch * nx * ny doubles; integrates to the norm).
+ * For (anti)symmetric states it is particle 2's as well.
+ *
+ * hom_conditional: conditional probability of particle 1 for particle 2 at
+ * the grid point (ix2, iy2) (caption of Fig. 2): out[x][y] =
+ * |psi(x, y, x2*, y2*)|^2, unnormalised (nx * ny doubles).
+ *
+ * hom_entanglement: spatial entanglement of Sec. V.  The 1D slice
+ * phi(x1, x2) = psi(x1, y1*, x2, y2*), with x1 in [x1_lo, x1_hi) (region T)
+ * and x2 in [x2_lo, x2_hi) (region B) at the y grid indices iy1, iy2, is
+ * renormalised; rho_T(x1, x1') = sum over x2 of phi(x1, x2) conj(phi(x1', x2))
+ * (Eq. reduced_density, read with phi*(x1', x2)); *entropy = -Tr rho_T ln rho_T
+ * (the von Neumann entropy; the printed formula drops the sign); *weight (if
+ * not NULL) = sum of |phi|^2 over the slice before renormalising.  The slice
+ * is gathered on the device; the eigenvalues come from a Jacobi
+ * diagonalisation on the host in FP64.  HOM_ERR_NUMERIC if the slice is zero.
+ *
+ * hom_vn_entropy: the same entropy for a slice given on the host (m1 * m2
+ * complex values as interleaved doubles, row-major); needs no GPU. */
+hom_status hom_marginal(hom_ctx* ctx, double* out);
+hom_status hom_conditional(hom_ctx* ctx, int32_t b, int32_t ix2, int32_t iy2, double* out);
+hom_status hom_entanglement(hom_ctx* ctx, int32_t b, int32_t iy1, int32_t iy2, int32_t x1_lo, int32_t x1_hi,
+                            int32_t x2_lo, int32_t x2_hi, double* entropy, double* weight);
+hom_status hom_vn_entropy(const double* phi, int32_t m1, int32_t m2, double* entropy, double* weight);
+
 /* Norm and bunching probability of a batch of states, for callers that
  * cannot allocate device memory: code that was handed the state in a buffer
  * it does not own (another framework's tensor, a slice of a pool) and runs

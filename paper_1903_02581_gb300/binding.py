@@ -98,6 +98,15 @@ def lib() -> ctypes.CDLL:
     L.hom_autotune_info.restype = ctypes.c_int
     L.hom_autotune_set.argtypes = [vp, P(ctypes.c_int32)]
     L.hom_autotune_set.restype = ctypes.c_int
+    L.hom_marginal.argtypes = [vp, P(ctypes.c_double)]
+    L.hom_marginal.restype = ctypes.c_int
+    L.hom_conditional.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double)]
+    L.hom_conditional.restype = ctypes.c_int
+    L.hom_entanglement.argtypes = [vp] + [ctypes.c_int32] * 7 + [P(ctypes.c_double), P(ctypes.c_double)]
+    L.hom_entanglement.restype = ctypes.c_int
+    L.hom_vn_entropy.argtypes = [P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double),
+                                 P(ctypes.c_double)]
+    L.hom_vn_entropy.restype = ctypes.c_int
     L.hom_last_error.argtypes = [vp]
     L.hom_last_error.restype = ctypes.c_char_p
     L.hom_destroy.argtypes = [vp]
@@ -151,6 +160,39 @@ def hom_backward(ctx, batch: int, nsteps: int, K: int):
     grad = (ctypes.c_double * (3 * batch))()
     _check(lib().hom_backward(ctx, nsteps, K, loss, grad), ctx)
     return np.array(loss[:]), np.array(grad[:]).reshape(batch, 3)
+
+
+def hom_marginal(ctx, batch: int, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((batch, nx, ny), dtype=np.float64)
+    _check(lib().hom_marginal(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+    return out
+
+
+def hom_conditional(ctx, b: int, ix2: int, iy2: int, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((nx, ny), dtype=np.float64)
+    _check(lib().hom_conditional(ctx, b, ix2, iy2, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+    return out
+
+
+def hom_entanglement(ctx, b: int, iy1: int, iy2: int, x1_range, x2_range) -> tuple[float, float]:
+    s = ctypes.c_double()
+    w = ctypes.c_double()
+    _check(lib().hom_entanglement(ctx, b, iy1, iy2, x1_range[0], x1_range[1], x2_range[0], x2_range[1],
+                                  ctypes.byref(s), ctypes.byref(w)), ctx)
+    return s.value, w.value
+
+
+def hom_vn_entropy(phi: np.ndarray) -> tuple[float, float]:
+    a = np.ascontiguousarray(phi, dtype=np.complex128)
+    if a.ndim != 2:
+        raise ValueError("phi must be a 2D array")
+    s = ctypes.c_double()
+    w = ctypes.c_double()
+    st = lib().hom_vn_entropy(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.shape[0], a.shape[1],
+                              ctypes.byref(s), ctypes.byref(w))
+    if st != HOM_OK:
+        raise HomError(st, "hom_vn_entropy failed")
+    return s.value, w.value
 
 
 def hom_copy_state(ctx, b: int, host: np.ndarray, to_device: bool):
@@ -267,6 +309,18 @@ class Propagator:
 
     def backward(self, nsteps: int, K: int):
         return hom_backward(self.ctx, self.batch, nsteps, K)
+
+    def marginal(self) -> np.ndarray:
+        """Unconditional probability density of particle 1, [batch][nx][ny]."""
+        return hom_marginal(self.ctx, self.batch, self.w["nx"], self.w["ny"])
+
+    def conditional(self, b: int, ix2: int, iy2: int) -> np.ndarray:
+        """|psi(x1, y1, x2*, y2*)|^2 of simulation b, [nx][ny]."""
+        return hom_conditional(self.ctx, b, ix2, iy2, self.w["nx"], self.w["ny"])
+
+    def entanglement(self, b: int, iy1: int, iy2: int, x1_range, x2_range) -> tuple[float, float]:
+        """(von Neumann entropy, slice weight) of the slice at (y1*, y2*)."""
+        return hom_entanglement(self.ctx, b, iy1, iy2, x1_range, x2_range)
 
     def get_state(self, b: int = 0) -> np.ndarray:
         nx, ny = self.w["nx"], self.w["ny"]

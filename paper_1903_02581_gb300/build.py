@@ -19,6 +19,7 @@ LIB = os.path.join(LIBDIR, "libhom.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 UNITS = ["hom_api.cu", "hom_kern_c64.cu", "hom_kern_c64_rows.cu", "hom_kern_c128.cu", "hom_kern_c128_rows.cu",
+         "hom_observe.cu",
          "hom_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -51,7 +51,7 @@ adj_mask(const C* __restrict__ psi, C* __restrict__ lam, double* __restrict__ sl
     const C v = p[i];
     if (same) {
       l[i] = v;
-      s += (double)cnorm2(v);
+      s += cnorm2_d(v);
     } else {
       l[i] = C{0, 0};
     }

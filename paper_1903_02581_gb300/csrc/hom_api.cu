@@ -795,6 +795,82 @@ hom_status measure_launch(hom_ctx* c) {
 
 }  // namespace
 
+// Eigenvalues of a Hermitian matrix (row-major, overwritten) by the cyclic
+// Jacobi method: each rotation first turns the (p, q) element real with a
+// diagonal phase, then zeroes it with a real plane rotation.  Both are unitary
+// similarities, so the spectrum is kept; the off-diagonal mass falls
+// quadratically once small.
+std::vector<double> hermitian_eigenvalues(std::vector<cd>& a, int n) {
+  auto at = [&](int i, int j) -> cd& { return a[(size_t)i * n + j]; };
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) (i == j ? diag : off) += std::norm(at(i, j));
+    if (off <= 1e-32 * diag || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const cd apq = at(p, q);
+        const double r = std::abs(apq);
+        if (r == 0.0) continue;
+        const cd e = apq / r;
+        const double app = at(p, p).real(), aqq = at(q, q).real();
+        const double th = (aqq - app) / (2.0 * r);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {
+          if (k == p || k == q) continue;
+          const cd bkp = at(k, p), bkq = at(k, q) * std::conj(e);
+          const cd nkp = c * bkp - sn * bkq, nkq = sn * bkp + c * bkq;
+          at(k, p) = nkp;
+          at(p, k) = std::conj(nkp);
+          at(k, q) = nkq;
+          at(q, k) = std::conj(nkq);
+        }
+        at(p, p) = cd(app - t * r, 0.0);
+        at(q, q) = cd(aqq + t * r, 0.0);
+        at(p, q) = at(q, p) = cd(0.0, 0.0);
+      }
+    }
+  }
+  std::vector<double> ev(n);
+  for (int i = 0; i < n; ++i) ev[i] = at(i, i).real();
+  return ev;
+}
+
+// Von Neumann entropy of the renormalised slice phi (m1 x m2, row-major):
+// the eigenvalues of phi phi^dagger and of phi^dagger phi are the same apart
+// from zeros, so the smaller Gram matrix is diagonalised.  Returns false if
+// the slice is zero.
+bool slice_entropy(const cd* phi, int m1, int m2, double* entropy, double* weight) {
+  double w = 0.0;
+  for (size_t k = 0; k < (size_t)m1 * m2; ++k) w += std::norm(phi[k]);
+  if (weight) *weight = w;
+  if (!(w > 0.0) || !std::isfinite(w)) return false;
+  const bool rows = m1 <= m2;
+  const int g = rows ? m1 : m2;
+  std::vector<cd> gram((size_t)g * g);
+  for (int i = 0; i < g; ++i) {
+    for (int j = i; j < g; ++j) {
+      cd acc(0.0, 0.0);
+      if (rows) {
+        for (int k = 0; k < m2; ++k) acc += phi[(size_t)i * m2 + k] * std::conj(phi[(size_t)j * m2 + k]);
+      } else {
+        for (int k = 0; k < m1; ++k) acc += std::conj(phi[(size_t)k * m2 + i]) * phi[(size_t)k * m2 + j];
+      }
+      acc /= w;
+      gram[(size_t)i * g + j] = acc;
+      gram[(size_t)j * g + i] = std::conj(acc);
+    }
+    gram[(size_t)i * g + i] = cd(gram[(size_t)i * g + i].real(), 0.0);
+  }
+  const std::vector<double> ev = hermitian_eigenvalues(gram, g);
+  double sum = 0.0;
+  for (double l : ev)
+    if (l > 0.0) sum -= l * std::log(l);
+  *entropy = sum;
+  return true;
+}
+
 extern "C" {
 
 size_t hom_state_bytes(const hom_params* p) {
@@ -1100,6 +1176,74 @@ hom_status hom_copy_state(hom_ctx* c, int32_t b, void* host, size_t bytes, int32
   }
   HOM_CUDA(c, cudaStreamSynchronize(c->stream));
   return HOM_OK;
+}
+
+hom_status hom_marginal(hom_ctx* c, double* out) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  if (!out) return fail(c, HOM_ERR_ARG, "out is NULL");
+  const hom_params& p = c->p;
+  const int n = p.nx * p.ny;
+  double* d = reinterpret_cast<double*>(c->ws + c->L.pong);
+  HOM_CUDA(c, p.prec == HOM_C128 ? hom::launch_marginal<double>(c->state, n, p.batch, d, c->stream)
+                                 : hom::launch_marginal<float>(c->state, n, p.batch, d, c->stream));
+  const size_t cnt = (size_t)p.batch * n;
+  HOM_CUDA(c, cudaMemcpyAsync(out, d, cnt * 8, cudaMemcpyDeviceToHost, c->stream));
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double a = p.dx * p.dy;
+  for (size_t k = 0; k < cnt; ++k) out[k] *= a;
+  return HOM_OK;
+}
+
+hom_status hom_conditional(hom_ctx* c, int32_t b, int32_t ix2, int32_t iy2, double* out) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  const hom_params& p = c->p;
+  if (!out) return fail(c, HOM_ERR_ARG, "out is NULL");
+  if (b < 0 || b >= p.batch) return fail(c, HOM_ERR_ARG, "simulation index %d out of range", b);
+  if (ix2 < 0 || ix2 >= p.nx || iy2 < 0 || iy2 >= p.ny)
+    return fail(c, HOM_ERR_ARG, "grid point (%d, %d) outside %d x %d", ix2, iy2, p.nx, p.ny);
+  const int n = p.nx * p.ny;
+  const char* st = c->state + (size_t)b * n * n * elem_bytes(p);
+  double* d = reinterpret_cast<double*>(c->ws + c->L.pong);
+  const int col = ix2 * p.ny + iy2;
+  HOM_CUDA(c, p.prec == HOM_C128 ? hom::launch_gather<double>(st, n, 0, 1, n, col, 0, 1, nullptr, d, c->stream)
+                                 : hom::launch_gather<float>(st, n, 0, 1, n, col, 0, 1, nullptr, d, c->stream));
+  HOM_CUDA(c, cudaMemcpyAsync(out, d, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
+hom_status hom_entanglement(hom_ctx* c, int32_t b, int32_t iy1, int32_t iy2, int32_t x1_lo, int32_t x1_hi,
+                            int32_t x2_lo, int32_t x2_hi, double* entropy, double* weight) {
+  hom_status s = enter(c);
+  if (s != HOM_OK) return s;
+  const hom_params& p = c->p;
+  if (!entropy) return fail(c, HOM_ERR_ARG, "entropy is NULL");
+  if (b < 0 || b >= p.batch) return fail(c, HOM_ERR_ARG, "simulation index %d out of range", b);
+  if (iy1 < 0 || iy1 >= p.ny || iy2 < 0 || iy2 >= p.ny) return fail(c, HOM_ERR_ARG, "y index out of range");
+  if (x1_lo < 0 || x1_hi > p.nx || x1_lo >= x1_hi || x2_lo < 0 || x2_hi > p.nx || x2_lo >= x2_hi)
+    return fail(c, HOM_ERR_ARG, "x ranges must satisfy 0 <= lo < hi <= nx");
+  const int n = p.nx * p.ny, m1 = x1_hi - x1_lo, m2 = x2_hi - x2_lo;
+  const char* st = c->state + (size_t)b * n * n * elem_bytes(p);
+  double2* d = reinterpret_cast<double2*>(c->ws + c->L.pong);
+  const int r0 = x1_lo * p.ny + iy1, c0 = x2_lo * p.ny + iy2;
+  HOM_CUDA(c, p.prec == HOM_C128
+                  ? hom::launch_gather<double>(st, n, r0, p.ny, m1, c0, p.ny, m2, d, nullptr, c->stream)
+                  : hom::launch_gather<float>(st, n, r0, p.ny, m1, c0, p.ny, m2, d, nullptr, c->stream));
+  std::vector<cd> phi((size_t)m1 * m2);
+  HOM_CUDA(c, cudaMemcpyAsync(phi.data(), d, phi.size() * 16, cudaMemcpyDeviceToHost, c->stream));
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!slice_entropy(phi.data(), m1, m2, entropy, weight))
+    return fail(c, HOM_ERR_NUMERIC, "the slice is zero or not finite");
+  return HOM_OK;
+}
+
+hom_status hom_vn_entropy(const double* phi, int32_t m1, int32_t m2, double* entropy, double* weight) {
+  if (!phi || !entropy || m1 < 1 || m2 < 1) return HOM_ERR_ARG;
+  std::vector<cd> a((size_t)m1 * m2);
+  for (size_t k = 0; k < a.size(); ++k) a[k] = cd(phi[2 * k], phi[2 * k + 1]);
+  return slice_entropy(a.data(), m1, m2, entropy, weight) ? HOM_OK : HOM_ERR_NUMERIC;
 }
 
 const char* hom_last_error(const hom_ctx* c) {

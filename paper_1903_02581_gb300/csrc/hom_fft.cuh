@@ -39,6 +39,11 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
 template <typename C> __device__ __forceinline__ typename Re<C>::type cnorm2(C a) {
   return a.x * a.x + a.y * a.y;
 }
+// |a|^2 in FP64 (exact for an FP32 a: each square fits a double), for the
+// FP64 reductions of the observables.
+template <typename C> __device__ __forceinline__ double cnorm2_d(C a) {
+  return fma((double)a.x, (double)a.x, (double)a.y * (double)a.y);
+}
 template <typename C> __device__ __forceinline__ C ldg(const C* p) { return __ldg(p); }
 
 // cos and sin of 2*pi*j/16, j = 0..15 (exact values of the 16th roots of unity).

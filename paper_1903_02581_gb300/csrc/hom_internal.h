@@ -43,6 +43,18 @@ template <typename T>
 cudaError_t launch_kinetic_t(int nx, int ny, int variant, const PassArgsT<typename Cx<T>::type>& a, int batch,
                              cudaStream_t s);
 
+// out[b * n + r1] = sum over r2 of |psi[b][r1][r2]|^2 in FP64, for batch states
+// of [n][n] (hom_observe.cuh).
+template <typename T>
+cudaError_t launch_marginal(const void* psi, int n, int batch, double* out, cudaStream_t s);
+
+// out[i * ncols + j] (FP64 complex) and mag2 (|.|^2) of the elements
+// psi[(row0 + i * rstride) * n + col0 + j * cstride] of one [n][n] state;
+// either output may be null.
+template <typename T>
+cudaError_t launch_gather(const void* psi, int n, int row0, int rstride, int nrows, int col0, int cstride, int ncols,
+                          double2* out, double* mag2, cudaStream_t s);
+
 // dst = transpose of each [n][n] state of src (batch states).
 template <typename T>
 cudaError_t launch_transpose(const void* src, void* dst, int n, int batch, cudaStream_t s);

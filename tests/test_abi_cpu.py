@@ -1,9 +1,11 @@
 """Host-side checks of libhom that need no GPU: it builds, loads, exports every
-function include/hom.h declares, sizes buffers, and rejects bad arguments
-before touching the device."""
+function include/hom.h declares, sizes buffers, rejects bad arguments before
+touching the device, and computes slice entropies on the host (the one
+entry point with no device work)."""
 
 import ctypes
 
+import numpy as np
 import pytest
 
 from paper_1903_02581_gb300 import binding as H
@@ -70,3 +72,34 @@ def test_null_context_calls(lib):
     assert lib.hom_step(None, 1) == H.HOM_ERR_ARG
     assert lib.hom_observables(None, None) == H.HOM_ERR_ARG
     lib.hom_destroy(None)
+
+
+# --- host-side entropy of a slice (no GPU) -----------------------------------
+
+def test_vn_entropy_closed_forms_and_oracle(lib):
+    import math
+
+    from oracle import hom_oracle as O
+
+    rng = np.random.default_rng(3)
+    for probs in [(1.0,), (0.5, 0.5), (0.6, 0.3, 0.1)]:
+        u, _ = np.linalg.qr(rng.standard_normal((7, 7)) + 1j * rng.standard_normal((7, 7)))
+        v, _ = np.linalg.qr(rng.standard_normal((11, 11)) + 1j * rng.standard_normal((11, 11)))
+        phi = 0.8 * sum(math.sqrt(p) * np.outer(u[:, k], v[:, k]) for k, p in enumerate(probs))
+        for a in (phi, phi.T.copy()):
+            s, w = H.hom_vn_entropy(a)
+            assert abs(s + sum(p * math.log(p) for p in probs)) <= 1e-12
+            assert abs(w - 0.64) <= 1e-13
+    # a generic slice: the same entropy as the oracle (numpy eigvalsh of rho_T)
+    psi = W.random_state((12, 3, 12, 3), seed=9)
+    s_ref, w_ref = O.entanglement_entropy(psi, 1, 2, (2, 10), (0, 12))
+    s, w = H.hom_vn_entropy(psi[2:10, 1, 0:12, 2])
+    assert abs(s - s_ref) <= 1e-12 and abs(w - w_ref) <= 1e-12 * w_ref
+
+
+def test_vn_entropy_errors(lib):
+    with pytest.raises(H.HomError) as e:
+        H.hom_vn_entropy(np.zeros((4, 5), dtype=np.complex128))
+    assert e.value.status == H.HOM_ERR_NUMERIC
+    s = ctypes.c_double()
+    assert lib.hom_vn_entropy(None, 2, 2, ctypes.byref(s), None) == H.HOM_ERR_ARG
