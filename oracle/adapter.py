@@ -13,7 +13,8 @@ def model_for(w: dict, sim: dict | None = None) -> O.Model:
     sim = sim or {}
     return O.Model(nx=w["nx"], ny=w["ny"], dx=w["dx"], dy=w["dy"], B=w["B"], omega=w["omega"],
                    dt=w["dt"], qpc_h=sim.get("qpc_h", w["qpc_h"]), qpc_w=sim.get("qpc_w", w["qpc_w"]),
-                   qpc_x0=w.get("qpc_x0", 0.0), lam=sim.get("lam", w["lam"]), soft=w["soft"])
+                   qpc_x0=w.get("qpc_x0", 0.0), lam=sim.get("lam", w["lam"]), soft=w["soft"],
+                   screen=w.get("screen", 0.0))
 
 
 def packet_k0(m: O.Model, pk: dict) -> float:

@@ -17,7 +17,8 @@ What is followed, by passage
   of the 4D two-particle wavefunction with 2D Fourier transforms over the axis
   pairs (x1,x2) and (y1,y2), kinetic phases diagonal in the transformed
   representation and the potential phase diagonal in real space.
-* Eq. (coulomb): V12 = lambda / sqrt(|r1-r2|^2 + a^2).
+* Eq. (coulomb): V12 = lambda / sqrt(|r1-r2|^2 + a^2), and its screened form
+  Eq. (screenedCoulomb) with the damping exp(-|r1-r2| / sigma_c).
 * Eq. (twopstate): Slater determinant of two single-particle packets.
 * Eq. (singlepwp) and Eq. (H_effective): a packet is a Gaussian-weighted sum
   of edge eigenstates e^{ik x} phi_k(y) of the confined Landau problem.
@@ -107,6 +108,7 @@ class Model:
     qpc_x0: float = 0.0
     lam: float = 1.0            # Coulomb strength, Eq. (coulomb)
     soft: float = 0.5           # Coulomb softening (the paper's thickness d)
+    screen: float = 0.0         # screening length sigma_c of Eq. (screenedCoulomb); 0: none
 
     @property
     def dV(self) -> float:
@@ -164,13 +166,19 @@ def v1(m: Model, h: float | None = None, w: float | None = None) -> np.ndarray:
 
 
 def v12(m: Model, lam: float | None = None) -> np.ndarray:
-    """Coulomb interaction V12[x1, y1, x2, y2], Eq. (coulomb) with thickness a."""
+    """Coulomb interaction V12[x1, y1, x2, y2], Eq. (coulomb) with thickness a;
+    with m.screen = sigma_c > 0 the exponential damping exp(-|r1 - r2| / sigma_c)
+    of Eq. (screenedCoulomb), whose exponent has no thickness term."""
     lam = m.lam if lam is None else lam
     x = coords(m.nx, m.dx)
     y = coords(m.ny, m.dy)
     ddx = x[:, None, None, None] - x[None, None, :, None]
     ddy = y[None, :, None, None] - y[None, None, None, :]
-    return lam / np.sqrt(ddx ** 2 + ddy ** 2 + m.soft ** 2)
+    r2 = ddx ** 2 + ddy ** 2
+    v = lam / np.sqrt(r2 + m.soft ** 2)
+    if m.screen > 0.0:
+        v = v * np.exp(-np.sqrt(r2) / m.screen)
+    return v
 
 
 def v_total(m: Model, h=None, w=None, lam=None) -> np.ndarray:
