@@ -66,7 +66,17 @@ typedef struct {
   double coul_lambda, coul_soft;
   int32_t observe_every;   /* informational: caller's observation cadence */
   int32_t ckpt_slots;
+  double coul_screen;      /* sigma_c of Eq. screenedCoulomb: V12 gains exp(-|r1-r2|/sigma_c); 0 = none */
+  int32_t split;           /* HOM_STRANG (default) or HOM_LIE */
+  int32_t reserved;        /* must be 0 */
 } hom_params;
+
+/* Splitting of one time step.  HOM_STRANG: V/2 . Fx^-1 Tx/2 Fy^-1 Ty Fy Tx/2
+ * Fx . V/2 (second order; the path the tolerances are stated for).  HOM_LIE:
+ * the first-order product printed in Eq. evoloperat, applied right to left as
+ * the x kinetic phase (full step), the y kinetic phase, then the potential
+ * (full step).  hom_backward needs HOM_STRANG. */
+enum { HOM_STRANG = 0, HOM_LIE = 1 };
 
 /* One edge packet (Eq. singlepwp): centre x0, width sigma (standard
  * deviation of |psi|^2 along x), and either the energy of the central

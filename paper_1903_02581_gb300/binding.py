@@ -18,6 +18,7 @@ from . import build as _build
 
 HOM_OK, HOM_ERR_ARG, HOM_ERR_STATE, HOM_ERR_CUDA, HOM_ERR_NOMEM, HOM_ERR_TIMEOUT, HOM_ERR_NUMERIC = range(7)
 HOM_C64, HOM_C128 = 0, 1
+HOM_STRANG, HOM_LIE = 0, 1
 STATUS_NAMES = ["HOM_OK", "HOM_ERR_ARG", "HOM_ERR_STATE", "HOM_ERR_CUDA", "HOM_ERR_NOMEM",
                 "HOM_ERR_TIMEOUT", "HOM_ERR_NUMERIC"]
 
@@ -29,7 +30,8 @@ class hom_params(ctypes.Structure):
                 ("omega_y", ctypes.c_double), ("dt", ctypes.c_double),
                 ("qpc_h", ctypes.c_double), ("qpc_w", ctypes.c_double), ("qpc_x0", ctypes.c_double),
                 ("coul_lambda", ctypes.c_double), ("coul_soft", ctypes.c_double),
-                ("observe_every", ctypes.c_int32), ("ckpt_slots", ctypes.c_int32)]
+                ("observe_every", ctypes.c_int32), ("ckpt_slots", ctypes.c_int32),
+                ("coul_screen", ctypes.c_double), ("split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class hom_packet(ctypes.Structure):
@@ -256,6 +258,9 @@ def make_params(w: dict, batch: int | None = None, ckpt_slots: int = 0, dt: floa
     p.coul_lambda, p.coul_soft = w["lam"], w["soft"]
     p.observe_every = w.get("observe_every", 0)
     p.ckpt_slots = ckpt_slots
+    p.coul_screen = w.get("screen", 0.0)
+    p.split = HOM_LIE if w.get("split", "strang") == "lie" else HOM_STRANG
+    p.reserved = 0
     return p
 
 

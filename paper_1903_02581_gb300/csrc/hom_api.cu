@@ -114,6 +114,14 @@ bool sizes_ok(const hom_params& p, std::string* why) {
     if (why) *why = "ckpt_slots must be >= 0";
     return false;
   }
+  if (!(p.coul_screen >= 0.0) || !std::isfinite(p.coul_screen)) {
+    if (why) *why = "coul_screen must be finite and >= 0 (0: no screening)";
+    return false;
+  }
+  if ((p.split != HOM_STRANG && p.split != HOM_LIE) || p.reserved != 0) {
+    if (why) *why = "split must be HOM_STRANG or HOM_LIE, reserved 0";
+    return false;
+  }
   return true;
 }
 
@@ -277,9 +285,12 @@ hom_status build_shared_tables(hom_ctx* c) {
       for (int j = 0; j < ny; ++j) {
         const double y = coord(ny, p.dy, j);
         const double t = 0.5 * (k - p.B * y) * (k - p.B * y);
-        const cd q = phase_delta(0.5 * dt * t);      // e^{-i (dt/2) T_x} - 1
+        // Strang: e^{-i (dt/2) T_x} - 1 on both sides of the y sandwich;
+        // Lie: the full step e^{-i dt T_x} - 1 before it and nothing after
+        const bool lie = p.split == HOM_LIE;
+        const cd q = phase_delta((lie ? 1.0 : 0.5) * dt * t);
         put(qa, dbl, (size_t)px * ny + j, q);
-        put(qt, dbl, (size_t)j * nx + px, q);
+        put(qt, dbl, (size_t)j * nx + px, lie ? cd(0.0, 0.0) : q);
         if (sgn == 0) tx[(size_t)px * ny + j] = t;
       }
     }
@@ -336,9 +347,10 @@ hom_status build_sim_tables(hom_ctx* c, int b) {
   }
   for (int ddx = -(nx - 1); ddx <= nx - 1; ++ddx) {
     for (int ddy = -(ny - 1); ddy <= ny - 1; ++ddy) {
-      const double rx = ddx * p.dx, ry = ddy * p.dy;
-      v12[(size_t)(ddx + nx - 1) * dny + (ddy + ny - 1)] =
-          sp.lam / std::sqrt(rx * rx + ry * ry + p.coul_soft * p.coul_soft);
+      const double rx = ddx * p.dx, ry = ddy * p.dy, r2 = rx * rx + ry * ry;
+      double v = sp.lam / std::sqrt(r2 + p.coul_soft * p.coul_soft);
+      if (p.coul_screen > 0.0) v *= std::exp(-std::sqrt(r2) / p.coul_screen);   // Eq. screenedCoulomb
+      v12[(size_t)(ddx + nx - 1) * dny + (ddy + ny - 1)] = v;
     }
   }
   std::vector<unsigned char> t1(n * eb), t12(D * eb);
@@ -487,6 +499,14 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   C* A = reinterpret_cast<C*>(psi);
   C* Bp = reinterpret_cast<C*>(c->ws + c->L.pong);
   bool in_a = true;
+  // The potential before the first step and after the last: dt/2 each
+  // (Strang), or none before and the full step after (Lie: K then V per step).
+  const bool lie = p.split == HOM_LIE;
+  const int v_first = lie ? 0 : 1;
+  const C* first1 = lie ? p1f : p1h;
+  const C* first12 = lie ? p12f : p12h;
+  const C* last1 = lie ? p1f : p1h;
+  const C* last12 = lie ? p12f : p12h;
   auto transposing = [&](C* src, C* dst, int v_load, int v_store, const C* t1, const C* t12) -> hom_status {
     hom::PassArgsT<C> a{};
     const char* d = reinterpret_cast<const char*>(dst);
@@ -562,7 +582,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     return HOM_OK;
   };
   if (c->strategy == 2) {
-    hom_status st = in_place_v(A, 1, 0, p1h, p12h);
+    hom_status st = in_place_v(A, v_first, 0, first1, first12);
     if (st != HOM_OK) return st;
     for (int s = 0; s < nsteps; ++s) {
       C* cur = in_a ? A : Bp;
@@ -572,7 +592,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
       if (s < nsteps - 1) {
         st = double_in_place(oth);
       } else {
-        st = in_place_v(oth, 0, 1, p1h, p12h);
+        st = in_place_v(oth, 0, 1, last1, last12);
         if (st == HOM_OK && !in_a) st = transpose(Bp, A);
       }
       if (st != HOM_OK) return st;
@@ -585,15 +605,15 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
       const bool last = s == nsteps - 1;
       C* cur = in_a ? A : Bp;
       C* oth = in_a ? Bp : A;
-      hom_status st = in_place_v(cur, 1, 0, s == 0 ? p1h : p1f, s == 0 ? p12h : p12f);
+      hom_status st = in_place_v(cur, s == 0 ? v_first : 1, 0, s == 0 ? first1 : p1f, s == 0 ? first12 : p12f);
       if (st != HOM_OK) return st;
       if ((st = transpose(cur, oth)) != HOM_OK) return st;
       in_a = !in_a;
       if (last && !in_a) {
         // the other particle's sandwich on the way back to the caller's layout
-        if ((st = transposing(Bp, A, 0, 1, p1h, p12h)) != HOM_OK) return st;
+        if ((st = transposing(Bp, A, 0, 1, last1, last12)) != HOM_OK) return st;
         in_a = true;
-      } else if ((st = in_place_v(oth, 0, last ? 1 : 0, p1h, p12h)) != HOM_OK) {
+      } else if ((st = in_place_v(oth, 0, last ? 1 : 0, last1, last12)) != HOM_OK) {
         return st;
       }
     }
@@ -601,14 +621,15 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
   }
   for (int s = 0; s < nsteps; ++s) {
     const bool last = s == nsteps - 1;
-    hom_status st = transposing(in_a ? A : Bp, in_a ? Bp : A, 1, 0, s == 0 ? p1h : p1f, s == 0 ? p12h : p12f);
+    hom_status st = transposing(in_a ? A : Bp, in_a ? Bp : A, s == 0 ? v_first : 1, 0, s == 0 ? first1 : p1f,
+                                s == 0 ? first12 : p12f);
     if (st != HOM_OK) return st;
     in_a = !in_a;
     if (last && !in_a) {
-      st = transposing(Bp, A, 0, 1, p1h, p12h);
+      st = transposing(Bp, A, 0, 1, last1, last12);
       in_a = true;
     } else {
-      st = in_place(in_a ? A : Bp, last ? 1 : 0, p1h, p12h);
+      st = in_place(in_a ? A : Bp, last ? 1 : 0, last1, last12);
     }
     if (st != HOM_OK) return st;
   }
@@ -1079,6 +1100,8 @@ hom_status hom_backward(hom_ctx* c, int32_t nsteps, int32_t K, double* loss, dou
   const hom_params& p = c->p;
   if (!loss || !grad) return fail(c, HOM_ERR_ARG, "loss and grad must be non-NULL");
   if (nsteps < 1 || K < 1) return fail(c, HOM_ERR_ARG, "nsteps and K must be >= 1");
+  if (p.split != HOM_STRANG)
+    return fail(c, HOM_ERR_ARG, "the adjoint needs the Strang split (S(dt)^dagger = S(-dt))");
   const int S = (nsteps + K - 1) / K;
   if (S > p.ckpt_slots)
     return fail(c, HOM_ERR_ARG, "%d checkpoints needed (nsteps=%d, K=%d) but ckpt_slots=%d", S, nsteps, K,

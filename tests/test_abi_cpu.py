@@ -41,7 +41,9 @@ def test_state_and_workspace_sizes(lib):
 
 @pytest.mark.parametrize("field,value", [("nx", 24), ("nx", 8), ("ny", 128), ("batch", 0),
                                          ("dx", 0.0), ("dt", 0.0), ("coul_soft", 0.0),
-                                         ("qpc_w", -1.0), ("prec", 7), ("ckpt_slots", -1)])
+                                         ("qpc_w", -1.0), ("prec", 7), ("ckpt_slots", -1),
+                                         ("coul_screen", -0.5), ("coul_screen", float("inf")),
+                                         ("split", 2), ("reserved", 1)])
 def test_invalid_params_rejected(lib, field, value):
     p = H.make_params(W.tiny())
     setattr(p, field, value)
