@@ -21,7 +21,9 @@ What is followed, by passage
   Eq. (screenedCoulomb) with the damping exp(-|r1-r2| / sigma_c).
 * Eq. (twopstate): Slater determinant of two single-particle packets.
 * Eq. (singlepwp) and Eq. (H_effective): a packet is a Gaussian-weighted sum
-  of edge eigenstates e^{ik x} phi_k(y) of the confined Landau problem.
+  of edge eigenstates e^{ik x} phi_k(y) of the confined Landau problem, in
+  closed form for the parabolic edge (R6) or numerically (R11).
+* Eqs. (pot_x) and (pot_xy): Fermi-function barriers (R10).
 * Eq. (p_bunching): bunching probability = probability that both particles
   are found on the same side of the beam splitter.
 * Captions of Fig. 2 and Fig. 3(b): conditional probability
@@ -65,6 +67,19 @@ R9  Spatial entanglement (Sec. V): the 1D slice phi(x1,x2) = psi(x1, y1*, x2, y2
     printed phi*(x2,x1') of Eq. reduced_density is read as phi*(x1',x2), the
     only form that is a density matrix); S = -Tr rho_T ln rho_T (the printed
     formula lacks the minus sign; S >= 0 is the von Neumann entropy).
+R10 Barriers of Eqs. (pot_x) and (pot_xy): F_tau(u) = 1 / (exp(u / tau) + 1)
+    with tau a length (the paper quotes tau = 3 nm).  With the axes of R1 the
+    QPC is two blocks, A = V_b F(x - xa) F(y - ya) (filling x < xa, y < ya)
+    and B = V_b F(xb - x) F(yb - y) (filling x > xb, y > yb); the factors at
+    -infinity of Eq. (pot_xy) are 1.  They add to the potential of R3.
+R11 Numerical edge states (Eq. H_effective, relabelled): phi_k(y) is the
+    lowest eigenvector of H_eff(k) = -1/2 d^2/dy^2 + 1/2 (k - B y)^2 +
+    1/2 omega^2 y^2 + V_wall(y) on the y grid, the second derivative being the
+    spectral one of the periodic grid (the operator the split step
+    propagates), V_wall(y) = V_b F_tau(s (y - y_w)) the one-sided barrier of
+    Eq. (pot_x) (s = +1: barrier below y_w, s = -1: above), normalised to
+    sum |phi|^2 dy = 1 with its largest component positive.  The packet of
+    Eq. (singlepwp) is then built as in R6 with these phi_k, from a given k0.
 R8  Adjoint: the Strang product is palindromic and each factor unitary, so
     S(dt)^dagger = S(-dt); the gradient of L = <psi_N|M|psi_N> with respect
     to a potential parameter theta is
@@ -109,6 +124,12 @@ class Model:
     lam: float = 1.0            # Coulomb strength, Eq. (coulomb)
     soft: float = 0.5           # Coulomb softening (the paper's thickness d)
     screen: float = 0.0         # screening length sigma_c of Eq. (screenedCoulomb); 0: none
+    fermi_vb: float = 0.0       # height V_b of the barrier blocks of Eq. (pot_xy); 0: none (R10)
+    fermi_tau: float = 1.0      # smoothness tau of F_tau, a length (R10)
+    fermi_xa: float = 0.0       # block A fills x < xa, y < ya
+    fermi_ya: float = 0.0
+    fermi_xb: float = 0.0       # block B fills x > xb, y > yb
+    fermi_yb: float = 0.0
 
     @property
     def dV(self) -> float:
@@ -156,13 +177,32 @@ def dft_pair(a: np.ndarray, axes: tuple[int, int], inverse: bool = False) -> np.
 # Operators (Appendix A with readings R1, R3; Eq. coulomb)
 # ----------------------------------------------------------------------------
 
+def fermi(u: np.ndarray, tau: float) -> np.ndarray:
+    """F_tau(u) = 1 / (exp(u / tau) + 1) of Eq. (pot_x) (R10), via the
+    library logistic function, which does not overflow."""
+    from scipy.special import expit
+    return expit(-np.asarray(u, dtype=np.float64) / tau)
+
+
+def v_fermi(m: Model) -> np.ndarray:
+    """The two barrier blocks of Eq. (pot_xy) on [x, y] (R10)."""
+    x = coords(m.nx, m.dx)[:, None]
+    y = coords(m.ny, m.dy)[None, :]
+    t = m.fermi_tau
+    return m.fermi_vb * (fermi(x - m.fermi_xa, t) * fermi(y - m.fermi_ya, t)
+                         + fermi(m.fermi_xb - x, t) * fermi(m.fermi_yb - y, t))
+
+
 def v1(m: Model, h: float | None = None, w: float | None = None) -> np.ndarray:
-    """Single-particle potential V1[x, y] (R3)."""
+    """Single-particle potential V1[x, y] (R3, plus the blocks of R10)."""
     h = m.qpc_h if h is None else h
     w = m.qpc_w if w is None else w
     x = coords(m.nx, m.dx)[:, None]
     y = coords(m.ny, m.dy)[None, :]
-    return 0.5 * m.omega ** 2 * y ** 2 + h * np.exp(-((x - m.qpc_x0) ** 2) / (2.0 * w ** 2))
+    v = 0.5 * m.omega ** 2 * y ** 2 + h * np.exp(-((x - m.qpc_x0) ** 2) / (2.0 * w ** 2))
+    if m.fermi_vb != 0.0:
+        v = v + v_fermi(m)
+    return v
 
 
 def v12(m: Model, lam: float | None = None) -> np.ndarray:
@@ -332,6 +372,44 @@ def edge_packet_dx0(m: Model, x0: float, sigma: float, k0: float) -> np.ndarray:
     dphi = plane @ ((-1j * k * wk)[:, None] * chi)
     nrm = math.sqrt(np.sum(np.abs(phi) ** 2) * m.dx * m.dy)
     return dphi / nrm
+
+
+def edge_hamiltonian(m: Model, k: float, wall_y: float = 0.0, wall_side: int = 1) -> np.ndarray:
+    """H_eff(k) on the y grid (R11), a real symmetric ny x ny matrix."""
+    y = coords(m.ny, m.dy)
+    ky = wavenumbers(m.ny, m.dy)
+    t = dft_matrix(m.ny, inverse=True) @ np.diag(0.5 * ky ** 2) @ dft_matrix(m.ny)
+    t = np.real(0.5 * (t + t.conj().T))
+    diag = 0.5 * (k - m.B * y) ** 2 + 0.5 * m.omega ** 2 * y ** 2
+    if m.fermi_vb != 0.0:
+        diag = diag + m.fermi_vb * fermi(wall_side * (y - wall_y), m.fermi_tau)
+    return t + np.diag(diag)
+
+
+def edge_state_numeric(m: Model, k: float, wall_y: float = 0.0, wall_side: int = 1) -> tuple[float, np.ndarray]:
+    """Lowest eigenpair of H_eff(k) by numpy.linalg.eigh (R11)."""
+    e, v = np.linalg.eigh(edge_hamiltonian(m, k, wall_y, wall_side))
+    phi = v[:, 0] / math.sqrt(np.sum(v[:, 0] ** 2) * m.dy)
+    if phi[np.argmax(np.abs(phi))] < 0:
+        phi = -phi
+    return float(e[0]), phi
+
+
+def edge_packet_numeric(m: Model, x0: float, sigma: float, k0: float,
+                        wall_y: float = 0.0, wall_side: int = 1) -> np.ndarray:
+    """Packet of Eq. (singlepwp) from numerical edge states (R11): weights
+    exp(-sigma^2 (k - k0)^2) over the grid wavenumbers, normalised.  Modes
+    whose weight is below 1e-300 are left out, as they cannot contribute."""
+    x = coords(m.nx, m.dx)
+    k = wavenumbers(m.nx, m.dx)
+    wk = np.exp(-(sigma ** 2) * (k - k0) ** 2)
+    chi = np.zeros((m.nx, m.ny))
+    for i in range(m.nx):
+        if wk[i] >= 1e-300:
+            chi[i] = edge_state_numeric(m, float(k[i]), wall_y, wall_side)[1]
+    plane = np.exp(1j * np.outer(x - x0, k))
+    phi = plane @ (wk[:, None] * chi)
+    return phi / math.sqrt(np.sum(np.abs(phi) ** 2) * m.dx * m.dy)
 
 
 def two_particle(alpha: np.ndarray, beta: np.ndarray, exch: int, dV: float) -> np.ndarray:

@@ -445,3 +445,76 @@ def test_entropy_of_slater_slice_is_ln2():
     psi[:, 1, :, 1] = (np.outer(u, v) - np.outer(v, u)) / math.sqrt(2.0)
     s, _ = O.entanglement_entropy(psi, 1, 1, (0, m.nx), (0, m.nx))
     assert abs(s - math.log(2.0)) <= 1e-12
+
+
+# --- the paper's barrier family and numerical edge states (R10, R11) ---------
+
+def test_fermi_function_closed_forms():
+    tau = 0.7
+    assert abs(O.fermi(0.0, tau) - 0.5) <= 1e-15
+    assert abs(O.fermi(tau * math.log(3.0), tau) - 0.25) <= 1e-15      # tau is a length
+    u = np.linspace(-9, 9, 37)
+    assert np.max(np.abs(O.fermi(u, tau) + O.fermi(-u, tau) - 1.0)) <= 1e-15
+    assert O.fermi(-50.0, tau) == pytest.approx(1.0) and O.fermi(50.0, tau) < 1e-30
+
+
+def test_barrier_blocks_of_pot_xy():
+    m = O.Model(nx=64, ny=32, dx=0.25, dy=0.25, omega=0.0, qpc_h=0.0, fermi_vb=3.0, fermi_tau=0.1,
+                fermi_xa=-1.0, fermi_ya=-0.5, fermi_xb=1.5, fermi_yb=1.0)
+    v = O.v1(m)
+    x = O.coords(m.nx, m.dx)
+    y = O.coords(m.ny, m.dy)
+    ix = lambda val: int(np.argmin(np.abs(x - val)))
+    iy = lambda val: int(np.argmin(np.abs(y - val)))
+    assert v[ix(-6.0), iy(-3.75)] == pytest.approx(3.0, rel=1e-9)         # inside block A
+    assert v[ix(6.0), iy(3.75)] == pytest.approx(3.0, rel=1e-9)           # inside block B
+    assert v[ix(-6.0), iy(3.75)] < 1e-9 and v[ix(6.0), iy(-3.75)] < 1e-9    # open quadrants
+    assert v[ix(0.25), iy(0.25)] < 1e-3                                   # the QPC gap
+    # a corner of a block sits at a quarter of the height
+    m2 = O.Model(nx=16, ny=16, dx=0.5, dy=0.5, omega=0.0, qpc_h=0.0, fermi_vb=2.0, fermi_tau=0.3,
+                 fermi_xa=O.coords(16, 0.5)[5], fermi_ya=O.coords(16, 0.5)[7], fermi_xb=99.0, fermi_yb=99.0)
+    assert O.v1(m2)[5, 7] == pytest.approx(0.5, rel=1e-12)
+
+
+@pytest.mark.parametrize("k", [-1.5, 0.0, 2.0])
+def test_numerical_edge_state_matches_closed_form(k):
+    m = O.Model(nx=32, ny=64, dx=0.5, dy=0.25, B=1.0, omega=1.0)
+    e, phi = O.edge_state_numeric(m, k)
+    om = math.sqrt(2.0)
+    assert abs(e - (0.5 * om + k * k / (2 * om ** 2))) <= 1e-12
+    y = O.coords(m.ny, m.dy)
+    chi = (om / math.pi) ** 0.25 * np.exp(-0.5 * om * (y - k / om ** 2) ** 2)
+    assert np.max(np.abs(phi - chi)) <= 1e-10
+
+
+def test_numerical_edge_state_pure_landau_level():
+    m = O.Model(nx=32, ny=64, dx=0.5, dy=0.25, B=1.5, omega=0.0)
+    for k in (-2.0, 0.5, 3.0):                                            # centre k/B inside the box
+        assert abs(O.edge_state_numeric(m, k)[0] - 0.75) <= 1e-11       # B/2
+
+
+def test_wall_side_convention():
+    m = O.Model(nx=32, ny=64, dx=0.5, dy=0.25, B=1.0, omega=1.0, fermi_vb=5.0, fermi_tau=0.2)
+    k = 2.0                                                               # centre y_k = 1
+    om = math.sqrt(2.0)
+    free = 0.5 * om + k * k / 4.0
+    y = O.coords(m.ny, m.dy)
+    chi = (om / math.pi) ** 0.25 * np.exp(-0.5 * om * (y - k / om ** 2) ** 2)
+    # first-order shift of the closed-form level by the smooth tail of a wall
+    # at y = -3: exp(-(y + 3)/tau) reaches the state; the second-order
+    # remainder is a few 1e-10, three orders below the shift itself
+    tail = float(np.sum(chi ** 2 * 5.0 / (np.exp((y + 3.0) / 0.2) + 1.0)) * m.dy)
+    assert 1e-7 < tail < 1e-5
+    # barrier below y = -3: the level rises by the tail only
+    assert abs(O.edge_state_numeric(m, k, wall_y=-3.0, wall_side=1)[0] - (free + tail)) <= 2e-9
+    # the same wall facing up covers the state: V_b minus the same tail
+    assert abs(O.edge_state_numeric(m, k, wall_y=-3.0, wall_side=-1)[0] - (free + 5.0 - tail)) <= 2e-9
+    # a wall through the state pushes the level up (variational bound)
+    assert O.edge_state_numeric(m, k, wall_y=1.0, wall_side=1)[0] > free + 0.05
+
+
+def test_numerical_packet_without_wall_is_the_closed_form_packet():
+    m = O.Model(nx=32, ny=64, dx=0.5, dy=0.25, B=1.0, omega=1.0)
+    a = O.edge_packet(m, -2.0, 1.3, 1.1)
+    b = O.edge_packet_numeric(m, -2.0, 1.3, 1.1)
+    assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(a))
