@@ -69,6 +69,13 @@ typedef struct {
   double coul_screen;      /* sigma_c of Eq. screenedCoulomb: V12 gains exp(-|r1-r2|/sigma_c); 0 = none */
   int32_t split;           /* HOM_STRANG (default) or HOM_LIE */
   int32_t reserved;        /* must be 0 */
+  /* Barrier blocks of Eq. pot_xy (axes relabelled as above), added to V1:
+   * fermi_vb [F(x - fermi_xa) F(y - fermi_ya) + F(fermi_xb - x) F(fermi_yb - y)]
+   * with F(u) = 1 / (exp(u / fermi_tau) + 1) (Eq. pot_x; tau a length), so
+   * block A fills x < xa, y < ya and block B x > xb, y > yb.  fermi_vb = 0:
+   * no blocks.  fermi_vb and fermi_tau also set the wall of numerical edge
+   * states (hom_packet.numeric). */
+  double fermi_vb, fermi_tau, fermi_xa, fermi_ya, fermi_xb, fermi_yb;
 } hom_params;
 
 /* Splitting of one time step.  HOM_STRANG: V/2 . Fx^-1 Tx/2 Fy^-1 Ty Fy Tx/2
@@ -82,10 +89,19 @@ enum { HOM_STRANG = 0, HOM_LIE = 1 };
  * deviation of |psi|^2 along x), and either the energy of the central
  * wavevector on the lowest hybrid level (by_k0 == 0; needs omega_y > 0 and
  * energy >= sqrt(B^2+omega_y^2)/2; dir = +1 moves towards +x, -1 towards -x)
- * or the central wavevector k0 itself (by_k0 != 0, dir ignored). */
+ * or the central wavevector k0 itself (by_k0 != 0, dir ignored).
+ * numeric == 0: the edge states are the closed-form lowest hybrid level of
+ * the parabolic edge.  numeric != 0 (needs by_k0): each edge state is the
+ * lowest eigenvector of Eq. H_effective on the y grid,
+ *   -1/2 d^2/dy^2 + 1/2 (k - B y)^2 + 1/2 omega_y^2 y^2 + V_wall(y),
+ * with the spectral second derivative of the grid and the one-sided wall of
+ * Eq. pot_x, V_wall(y) = fermi_vb F(wall_side (y - wall_y)) (wall_side +1:
+ * barrier below wall_y, -1: above), computed on the host in FP64 (Jacobi). */
 typedef struct {
   double x0, sigma, energy, k0;
   int32_t dir, by_k0;
+  int32_t numeric, wall_side;
+  double wall_y;
 } hom_packet;
 
 /* Observables of one simulation (host, FP64): norm = sum |psi|^2 dV;

@@ -31,12 +31,15 @@ class hom_params(ctypes.Structure):
                 ("qpc_h", ctypes.c_double), ("qpc_w", ctypes.c_double), ("qpc_x0", ctypes.c_double),
                 ("coul_lambda", ctypes.c_double), ("coul_soft", ctypes.c_double),
                 ("observe_every", ctypes.c_int32), ("ckpt_slots", ctypes.c_int32),
-                ("coul_screen", ctypes.c_double), ("split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("coul_screen", ctypes.c_double), ("split", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("fermi_vb", ctypes.c_double), ("fermi_tau", ctypes.c_double), ("fermi_xa", ctypes.c_double),
+                ("fermi_ya", ctypes.c_double), ("fermi_xb", ctypes.c_double), ("fermi_yb", ctypes.c_double)]
 
 
 class hom_packet(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_double), ("sigma", ctypes.c_double), ("energy", ctypes.c_double),
-                ("k0", ctypes.c_double), ("dir", ctypes.c_int32), ("by_k0", ctypes.c_int32)]
+                ("k0", ctypes.c_double), ("dir", ctypes.c_int32), ("by_k0", ctypes.c_int32),
+                ("numeric", ctypes.c_int32), ("wall_side", ctypes.c_int32), ("wall_y", ctypes.c_double)]
 
 
 class hom_obs(ctypes.Structure):
@@ -261,6 +264,9 @@ def make_params(w: dict, batch: int | None = None, ckpt_slots: int = 0, dt: floa
     p.coul_screen = w.get("screen", 0.0)
     p.split = HOM_LIE if w.get("split", "strang") == "lie" else HOM_STRANG
     p.reserved = 0
+    p.fermi_vb, p.fermi_tau = w.get("fermi_vb", 0.0), w.get("fermi_tau", 1.0)
+    p.fermi_xa, p.fermi_ya = w.get("fermi_xa", 0.0), w.get("fermi_ya", 0.0)
+    p.fermi_xb, p.fermi_yb = w.get("fermi_xb", 0.0), w.get("fermi_yb", 0.0)
     return p
 
 
@@ -268,6 +274,8 @@ def make_packet(d: dict) -> hom_packet:
     pk = hom_packet()
     pk.x0, pk.sigma, pk.energy, pk.k0 = d["x0"], d["sigma"], d.get("energy", 0.0), d.get("k0", 0.0)
     pk.dir, pk.by_k0 = d.get("dir", 1), 1 if d.get("by_k0", False) else 0
+    pk.numeric = 1 if d.get("numeric", False) else 0
+    pk.wall_side, pk.wall_y = d.get("wall_side", 1), d.get("wall_y", 0.0)
     return pk
 
 

@@ -61,6 +61,17 @@ double wavenumber(int n, double d, int m) {
 
 double coord(int n, double d, int j) { return (j - 0.5 * (n - 1)) * d; }
 
+// F_tau(u) = 1 / (exp(u / tau) + 1) of Eq. pot_x, written so that the
+// exponential never overflows.
+double fermi_fn(double u, double tau) {
+  const double z = u / tau;
+  if (z > 0.0) {
+    const double e = std::exp(-z);
+    return e / (1.0 + e);
+  }
+  return 1.0 / (1.0 + std::exp(z));
+}
+
 struct SimParams {
   double h, w, lam;
 };
@@ -120,6 +131,12 @@ bool sizes_ok(const hom_params& p, std::string* why) {
   }
   if ((p.split != HOM_STRANG && p.split != HOM_LIE) || p.reserved != 0) {
     if (why) *why = "split must be HOM_STRANG or HOM_LIE, reserved 0";
+    return false;
+  }
+  if (!std::isfinite(p.fermi_vb) || !std::isfinite(p.fermi_xa) || !std::isfinite(p.fermi_ya) ||
+      !std::isfinite(p.fermi_xb) || !std::isfinite(p.fermi_yb) ||
+      (p.fermi_vb != 0.0 && !(p.fermi_tau > 0.0 && std::isfinite(p.fermi_tau)))) {
+    if (why) *why = "fermi_* must be finite, and fermi_tau > 0 when fermi_vb != 0";
     return false;
   }
   return true;
@@ -342,7 +359,11 @@ hom_status build_sim_tables(hom_ctx* c, int b) {
     const double g = std::exp(-(x - p.qpc_x0) * (x - p.qpc_x0) / (2.0 * sp.w * sp.w));
     for (int iy = 0; iy < ny; ++iy) {
       const double y = coord(ny, p.dy, iy);
-      v1[(size_t)ix * ny + iy] = 0.5 * p.omega_y * p.omega_y * y * y + sp.h * g;
+      double v = 0.5 * p.omega_y * p.omega_y * y * y + sp.h * g;
+      if (p.fermi_vb != 0.0)   // the two blocks of Eq. pot_xy
+        v += p.fermi_vb * (fermi_fn(x - p.fermi_xa, p.fermi_tau) * fermi_fn(y - p.fermi_ya, p.fermi_tau) +
+                           fermi_fn(p.fermi_xb - x, p.fermi_tau) * fermi_fn(p.fermi_yb - y, p.fermi_tau));
+      v1[(size_t)ix * ny + iy] = v;
     }
   }
   for (int ddx = -(nx - 1); ddx <= nx - 1; ++ddx) {
@@ -380,6 +401,89 @@ hom_status build_sim_tables(hom_ctx* c, int b) {
 // level of the parabolic edge, (Omega/pi)^{1/4} e^{-Omega (y - k B/Omega^2)^2 / 2},
 // Omega^2 = B^2 + omega^2; normalised so that sum |psi|^2 dx dy = 1.  With
 // dpsi != nullptr also returns d psi / d x0 (the norm does not depend on x0).
+// Eigenpairs of a real symmetric matrix (row-major, overwritten) by the
+// cyclic Jacobi method, with the rotations accumulated into v (row-major,
+// columns are eigenvectors).  Returns the eigenvalues.
+std::vector<double> symmetric_eigen(std::vector<double>& a, int n, std::vector<double>& v) {
+  auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+  v.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) v[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) (i == j ? diag : off) += A(i, j) * A(i, j);
+    if (off <= 1e-32 * diag || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A(p, q);
+        if (apq == 0.0) continue;
+        const double th = (A(q, q) - A(p, p)) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          if (k == p || k == q) continue;
+          const double akp = A(k, p), akq = A(k, q);
+          A(k, p) = A(p, k) = cs * akp - sn * akq;
+          A(k, q) = A(q, k) = sn * akp + cs * akq;
+        }
+        A(p, p) -= t * apq;
+        A(q, q) += t * apq;
+        A(p, q) = A(q, p) = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
+          v[(size_t)k * n + p] = cs * vkp - sn * vkq;
+          v[(size_t)k * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+    }
+  }
+  std::vector<double> ev(n);
+  for (int i = 0; i < n; ++i) ev[i] = A(i, i);
+  return ev;
+}
+
+// Lowest eigenvector of Eq. H_effective at wavevector k on the y grid (see
+// hom_packet): normalised to sum phi^2 dy = 1, largest component positive.
+void numeric_edge_state(const hom_params& p, double k, double wall_y, int wall_side, std::vector<double>& phi) {
+  const int ny = p.ny;
+  std::vector<double> h((size_t)ny * ny), vec;
+  // spectral -1/2 d^2/dy^2: (1/ny) sum_m 1/2 k_m^2 cos(2 pi m (j - l) / ny)
+  std::vector<double> row(ny, 0.0);
+  for (int d = 0; d < ny; ++d) {
+    double acc = 0.0;
+    for (int m = 0; m < ny; ++m) {
+      const double km = wavenumber(ny, p.dy, m);
+      acc += 0.5 * km * km * std::cos(kTwoPi * (double)m * d / ny);
+    }
+    row[d] = acc / ny;
+  }
+  for (int j = 0; j < ny; ++j)
+    for (int l = 0; l < ny; ++l) h[(size_t)j * ny + l] = row[(j - l + ny) % ny];
+  for (int j = 0; j < ny; ++j) {
+    const double y = coord(ny, p.dy, j);
+    double d = 0.5 * (k - p.B * y) * (k - p.B * y) + 0.5 * p.omega_y * p.omega_y * y * y;
+    if (p.fermi_vb != 0.0) d += p.fermi_vb * fermi_fn(wall_side * (y - wall_y), p.fermi_tau);
+    h[(size_t)j * ny + j] += d;
+  }
+  const std::vector<double> ev = symmetric_eigen(h, ny, vec);
+  int lo = 0;
+  for (int i = 1; i < ny; ++i)
+    if (ev[i] < ev[lo]) lo = i;
+  phi.assign(ny, 0.0);
+  double nrm = 0.0, big = 0.0;
+  int at = 0;
+  for (int j = 0; j < ny; ++j) {
+    phi[j] = vec[(size_t)j * ny + lo];
+    nrm += phi[j] * phi[j];
+    if (std::fabs(phi[j]) > big) {
+      big = std::fabs(phi[j]);
+      at = j;
+    }
+  }
+  const double sc = (phi[at] < 0 ? -1.0 : 1.0) / std::sqrt(nrm * p.dy);
+  for (double& x : phi) x *= sc;
+}
+
 hom_status build_packet(hom_ctx* c, const hom_packet& pk, std::vector<cd>& psi, std::vector<cd>* dpsi) {
   const hom_params& p = c->p;
   const int nx = p.nx, ny = p.ny;
@@ -387,6 +491,11 @@ hom_status build_packet(hom_ctx* c, const hom_packet& pk, std::vector<cd>& psi, 
   if (!std::isfinite(pk.x0) || !(pk.sigma > 0) || !std::isfinite(pk.sigma))
     return fail(c, HOM_ERR_ARG, "packet needs finite x0 and sigma > 0");
   if (Om <= 0) return fail(c, HOM_ERR_ARG, "packets need B != 0 or omega_y != 0");
+  if (pk.numeric) {
+    if (!pk.by_k0) return fail(c, HOM_ERR_ARG, "numerical edge states need k0 (by_k0)");
+    if (pk.wall_side != 1 && pk.wall_side != -1) return fail(c, HOM_ERR_ARG, "wall_side must be +1 or -1");
+    if (!std::isfinite(pk.wall_y)) return fail(c, HOM_ERR_ARG, "wall_y must be finite");
+  }
   double k0;
   if (pk.by_k0) {
     if (!std::isfinite(pk.k0)) return fail(c, HOM_ERR_ARG, "k0 must be finite");
@@ -405,10 +514,14 @@ hom_status build_packet(hom_ctx* c, const hom_packet& pk, std::vector<cd>& psi, 
     const double k = wavenumber(nx, p.dx, m);
     const double wk = std::exp(-pk.sigma * pk.sigma * (k - k0) * (k - k0));
     if (wk < 1e-300) continue;
-    const double yk = k * p.B / (Om * Om);
-    for (int j = 0; j < ny; ++j) {
-      const double y = coord(ny, p.dy, j) - yk;
-      chi[j] = std::pow(Om / kPi, 0.25) * std::exp(-0.5 * Om * y * y);
+    if (pk.numeric) {
+      numeric_edge_state(p, k, pk.wall_y, pk.wall_side, chi);
+    } else {
+      const double yk = k * p.B / (Om * Om);
+      for (int j = 0; j < ny; ++j) {
+        const double y = coord(ny, p.dy, j) - yk;
+        chi[j] = std::pow(Om / kPi, 0.25) * std::exp(-0.5 * Om * y * y);
+      }
     }
     for (int ix = 0; ix < nx; ++ix) {
       const double arg = std::fmod(k * (coord(nx, p.dx, ix) - pk.x0), kTwoPi);

@@ -43,10 +43,13 @@ def test_state_and_workspace_sizes(lib):
                                          ("dx", 0.0), ("dt", 0.0), ("coul_soft", 0.0),
                                          ("qpc_w", -1.0), ("prec", 7), ("ckpt_slots", -1),
                                          ("coul_screen", -0.5), ("coul_screen", float("inf")),
-                                         ("split", 2), ("reserved", 1)])
+                                         ("split", 2), ("reserved", 1), ("fermi_xa", float("nan")),
+                                         ("fermi_vb", float("inf"))])
 def test_invalid_params_rejected(lib, field, value):
     p = H.make_params(W.tiny())
     setattr(p, field, value)
+    if field == "fermi_vb":
+        p.fermi_tau = 0.5
     assert H.hom_state_bytes(p) == 0
     assert H.hom_workspace_bytes(p) == 0
     ctx = ctypes.c_void_p()
@@ -105,3 +108,11 @@ def test_vn_entropy_errors(lib):
     assert e.value.status == H.HOM_ERR_NUMERIC
     s = ctypes.c_double()
     assert lib.hom_vn_entropy(None, 2, 2, ctypes.byref(s), None) == H.HOM_ERR_ARG
+
+
+def test_fermi_tau_needed_only_with_blocks(lib):
+    p = H.make_params(W.tiny())
+    p.fermi_tau = 0.0
+    assert H.hom_state_bytes(p) > 0                 # no blocks: tau unused
+    p.fermi_vb = 2.0
+    assert H.hom_state_bytes(p) == 0

@@ -1,6 +1,7 @@
-"""The screened Coulomb interaction (Eq. screenedCoulomb) and the paper's
-first-order Lie product (Eq. evoloperat as printed) on the GPU, against the
-FP64 oracle.
+"""The screened Coulomb interaction (Eq. screenedCoulomb), the paper's
+first-order Lie product (Eq. evoloperat as printed), the barrier blocks of
+Eq. pot_xy and numerical edge-state packets (Eq. H_effective) on the GPU,
+against the FP64 oracle.
 
 Tolerances are those of the Strang path: complex128 1e-10 and complex64 2e-5
 relative to the l2 norm of the state, observables 1e-11 (complex128).
@@ -99,3 +100,58 @@ def test_lie_rejects_adjoint():
     with pytest.raises(H().HomError) as e:
         pr.backward(4, 2)
     assert e.value.status == H().HOM_ERR_ARG
+
+
+# --- the barrier blocks of Eq. pot_xy and numerical edge states (Eq. H_effective)
+
+FERMI = dict(fermi_vb=2.5, fermi_tau=0.4, fermi_xa=-1.0, fermi_ya=-0.75, fermi_xb=1.0, fermi_yb=0.75)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_fermi_blocks_steps_and_energy(prec):
+    w = small_w(32, 16, prec, **FERMI)
+    pr = H().Propagator(w, init=False)
+    psi = W.random_state((32, 16, 32, 16), seed=91)
+    psi /= np.sqrt(np.sum(np.abs(psi) ** 2) * (w["dx"] * w["dy"]) ** 2)
+    pr.set_state(0, psi)
+    m = A.model_for(w, w["sims"][0])
+    assert m.fermi_vb == 2.5
+    s0 = psi.astype(np.complex64).astype(np.complex128) if prec == "c64" else psi
+    got = pr.observables()[0]["e_pot"]
+    ref = O.observables(s0, m)["e_pot"]
+    assert abs(got - ref) <= (1e-11 if prec == "c128" else 2e-6) * abs(ref)
+    pr.step(3)
+    assert rel_err(pr.get_state(0), O.propagate(s0, m, 3)) <= TOL[prec] * 0.1
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_numeric_edge_packets(prec):
+    w = small_w(32, 16, prec, **FERMI)
+    w["dt"] = 0.01
+    a = dict(W.packet(-3.0, 1.2, k0=1.5, by_k0=True), numeric=True, wall_y=-2.0, wall_side=1)
+    b = dict(W.packet(3.0, 1.2, k0=-1.5, by_k0=True), numeric=True, wall_y=2.0, wall_side=-1)
+    w["sims"][0].update(alpha=a, beta=b, exch=-1)
+    pr = H().Propagator(w)
+    ref0 = A.initial_state(w, w["sims"][0])
+    assert rel_err(pr.get_state(0), ref0) <= (1e-12 if prec == "c128" else 2e-7)
+    # the walls really change the packets
+    plain = dict(w["sims"][0], alpha=dict(a, numeric=False), beta=dict(b, numeric=False))
+    assert rel_err(pr.get_state(0), A.initial_state(w, plain)) > 1e-4
+    pr.step(5)
+    m = A.model_for(w, w["sims"][0])
+    # complex64: start the oracle from the rounded initial state
+    s0 = ref0 if prec == "c128" else H().Propagator(w).get_state(0).astype(np.complex128)
+    assert rel_err(pr.get_state(0), O.propagate(s0, m, 5)) <= TOL[prec] * 0.1
+
+
+def test_numeric_packet_errors():
+    w = small_w(16, 16, "c128", **FERMI)
+    pr = H().Propagator(w, init=False)
+    bad = H().make_packet(dict(W.packet(0.0, 1.0, 2.5, 1), numeric=True))      # numeric needs k0
+    good = H().make_packet(dict(W.packet(2.0, 1.0, k0=-1.0, by_k0=True), numeric=True, wall_side=1))
+    with pytest.raises(H().HomError) as e:
+        H().hom_init_packets(pr.ctx, 0, bad, good, -1)
+    assert e.value.status == H().HOM_ERR_ARG
+    side = H().make_packet(dict(W.packet(2.0, 1.0, k0=-1.0, by_k0=True), numeric=True, wall_side=0))
+    with pytest.raises(H().HomError):
+        H().hom_init_packets(pr.ctx, 0, good, side, -1)
