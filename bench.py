@@ -69,7 +69,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def _dft_flops(n: int) -> int:
+def _dft_flops(n: int, tw_general: int = 14) -> int:
     """FP32 flops of the in-register radix-2 DFT of length n (add, sub, mul = 1,
     FMA = 2): butterflies cost 4, a trivial twiddle (1, -i) 0, a (1 -+ i)/sqrt2
     twiddle 8 (two sums, two compensated scalings) and any other compensated
@@ -82,8 +82,8 @@ def _dft_flops(n: int) -> int:
     for k in range(1, n // 2):
         if 4 * k == n:
             continue
-        tw += 8 if 8 * k in (n, 3 * n) else 14
-    return 2 * _dft_flops(n // 2) + 4 * (n // 2) + tw
+        tw += 8 if 8 * k in (n, 3 * n) else tw_general
+    return 2 * _dft_flops(n // 2, tw_general) + 4 * (n // 2) + tw
 
 
 def _split(n: int):
@@ -91,26 +91,28 @@ def _split(n: int):
     return n1, n // n1
 
 
-def sandwich_flops(nx: int, ny: int) -> float:
+def sandwich_flops(nx: int, ny: int, fp64: bool = False) -> float:
     """Algorithmic FP32 flops per point of one kinetic sandwich as the kernels
     compute it: the x and y DFT stages, the compensated inter-stage twiddles
     (14), the T_x/2 and T_y phases applied as v + v*d (8 each) and the 1/(nx ny)
-    scale (2)."""
-    tw, ph = 14.0, 8.0
+    scale (2).  In FP64 a general twiddle is a plain complex product (6): the
+    low parts of the compensated pairs are FP32-only."""
+    tw, ph = (6.0 if fp64 else 14.0), 8.0
+    dft = (lambda n: _dft_flops(n, 6)) if fp64 else _dft_flops
     f = 0.0
     n1, n2 = _split(nx)
     if n2 == 1:
-        f += _dft_flops(nx) / nx + ph + _dft_flops(nx) / nx
+        f += dft(nx) / nx + ph + dft(nx) / nx
     else:
-        f += _dft_flops(n1) / n1 + tw * (n1 - 1) / n1 + _dft_flops(n2) / n2 + ph       # forward x, T_x/2
-        f += _dft_flops(n2) / n2 + tw * (n2 - 1) / n2 + _dft_flops(n1) / n1            # inverse x
+        f += dft(n1) / n1 + tw * (n1 - 1) / n1 + dft(n2) / n2 + ph       # forward x, T_x/2
+        f += dft(n2) / n2 + tw * (n2 - 1) / n2 + dft(n1) / n1            # inverse x
     m1, m2 = _split(ny)
     if m2 == 1:
-        f += 2 * _dft_flops(ny) / ny + ph + 2 + ph
+        f += 2 * dft(ny) / ny + ph + 2 + ph
     else:
-        f += _dft_flops(m1) / m1 + tw * (m1 - 1) / m1
-        f += 2 * _dft_flops(m2) / m2 + ph + tw * (m2 - 1) / m2
-        f += _dft_flops(m1) / m1 + 2 + ph
+        f += dft(m1) / m1 + tw * (m1 - 1) / m1
+        f += 2 * dft(m2) / m2 + ph + tw * (m2 - 1) / m2
+        f += dft(m1) / m1 + 2 + ph
     return f
 
 
@@ -295,6 +297,13 @@ def precision_study(device: str):
                      "max_rel_energy_drift": max(ed), "max_rel_energy_err_vs_oracle": max(eo)}
         pr.close()
     out["fp32_speedup"] = out["c64"]["updates_per_s"] / out["c128"]["updates_per_s"]
+    # complex128 is bound by the FP64 pipe: algorithmic FP64 flops per point
+    # per step (two sandwiches and the potential) against the nominal 1.25 TF/s
+    w = W.sweep32(prec="c128")
+    f64 = 2 * sandwich_flops(w["nx"], w["ny"], fp64=True) + VPHASE_FLOPS
+    out["c128"]["fp64_flops_per_point_step"] = f64
+    out["c128"]["fp64_tflops"] = out["c128"]["updates_per_s"] * f64 / 1e12
+    out["c128"]["fp64_frac_of_nominal_1.25_tflops"] = out["c128"]["fp64_tflops"] / 1.25
     return out
 
 

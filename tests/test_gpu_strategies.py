@@ -141,3 +141,35 @@ def test_autotune_reports_both_strategies():
         ref.step(2)
     ref.step(12)
     assert np.array_equal(ref.get_state(0).view(np.uint8), pr.get_state(0).view(np.uint8))
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_choices_bitwise_identical_batched(prec):
+    """Three simulations with different potentials: every choice gives the
+    same bits, and each simulation matches the oracle."""
+    from oracle import adapter as A
+    from oracle import hom_oracle as O
+
+    w = small_w(32, 16, prec)
+    w["sims"] = [dict(w["sims"][0], qpc_h=0.7 + 0.3 * b, lam=0.5 * b) for b in range(3)]
+    w["batch"] = 3
+    states = [W.random_state((32, 16, 32, 16), seed=200 + b) for b in range(3)]
+    out = {}
+    for ch in CHOICES:
+        pr = H().Propagator(w, init=False)
+        H().hom_autotune_set(pr.ctx, *ch)
+        for b in range(3):
+            pr.set_state(b, states[b])
+        pr.step(3)
+        out[ch] = [pr.get_state(b) for b in range(3)]
+        pr.close()
+    base = out[CHOICES[0]]
+    for ch in CHOICES[1:]:
+        for b in range(3):
+            assert np.array_equal(out[ch][b].view(np.uint8), base[b].view(np.uint8)), (ch, b)
+    for b in range(3):
+        m = A.model_for(w, w["sims"][b])
+        s0 = states[b].astype(np.complex64).astype(np.complex128) if prec == "c64" else states[b]
+        ref = O.propagate(s0, m, 3)
+        err = np.max(np.abs(base[b].astype(np.complex128) - ref)) / np.linalg.norm(ref.ravel())
+        assert err <= (1e-11 if prec == "c128" else 2e-6), (b, err)
