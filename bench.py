@@ -454,18 +454,23 @@ def gb300_arm(args):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        reps = []
         for _ in range(nrep):
+            ta = time.perf_counter()
             for b in range(batch):
-                H.hom_copy_state(pr.ctx, b, hview[b], to_device=True)
+                H.hom_copy_state(pr.ctx, b, hview[b], to_device=True)     # synchronises
+            tb = time.perf_counter()
             pr.step(args.inner)
-            pr.observables()
+            pr.observables()                                               # synchronises
+            reps.append([round((tb - ta) * 1e3, 2), round((time.perf_counter() - tb) * 1e3, 2)])
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         sec_t = torch.tensor([sec], dtype=torch.float64, device=f"cuda:{local}")
         if world > 1:
             dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
         e2e = {"value": world * batch * pts * args.inner * nrep / float(sec_t.item()), "unit": "updates/s",
-               "h2d_bytes_per_step": int(hview.nbytes), "d2h_bytes_per_step": 48 * batch, "steps": nrep}
+               "h2d_bytes_per_step": int(hview.nbytes), "d2h_bytes_per_step": 48 * batch, "steps": nrep,
+               "ms_copy_and_steps_per_rep": reps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
