@@ -305,7 +305,12 @@ class Propagator:
         self.device = torch.device(device)
         self.state = torch.empty((self.batch, n, n), dtype=self.dtype, device=self.device)
         self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        # A stream of its own (blocking, so that work on torch's default stream
+        # stays ordered with it): hom_step captures its launches into CUDA
+        # graphs, which the legacy default stream cannot hold.
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.state.record_stream(self.stream)
+        self.workspace.record_stream(self.stream)
         self.ctx = hom_create(self.params, self.state.data_ptr(), self.workspace.data_ptr(), wb,
                               self.stream.cuda_stream)
         if "sims" in w:
@@ -347,6 +352,7 @@ class Propagator:
 
     def close(self):
         if getattr(self, "ctx", None):
+            self.stream.synchronize()
             hom_destroy(self.ctx)
             self.ctx = None
 
