@@ -212,8 +212,10 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
     }
     __syncthreads();
   } else {
-    for (int it = tid; it < G * NX * N2; it += NT) {
-      const int px = it % NX, n2 = (it / NX) % N2, g = it / (NX * N2);
+    // the three register passes of a line: forward N1-point stage with its
+    // twiddle; N2-point stage, G, inverse N2-point stage, inverse twiddle;
+    // inverse N1-point stage with the scale and the closing T_x/2 phase
+    auto pass1 = [&](int g, int px, int n2) {
       C* row = sm + g * PS + px * RS;
       C v[N1];
 #pragma unroll
@@ -223,10 +225,8 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
       for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) row[N2 * k1 + n2] = v[k1];
-    }
-    __syncthreads();
-    for (int it = tid; it < G * NX * N1; it += NT) {
-      const int px = it % NX, k1 = (it / NX) % N1, g = it / (NX * N1);
+    };
+    auto pass2 = [&](int g, int px, int k1) {
       C* row = sm + g * PS + px * RS;
       C v[N2];
 #pragma unroll
@@ -239,10 +239,8 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
       for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_tw<true>(v[m1], tw, m1 * k1);
 #pragma unroll
       for (int m1 = 0; m1 < N2; ++m1) row[N2 * k1 + m1] = v[m1];
-    }
-    __syncthreads();
-    for (int it = tid; it < G * NX * N2; it += NT) {
-      const int px = it % NX, m1 = (it / NX) % N2, g = it / (NX * N2);
+    };
+    auto pass3 = [&](int g, int px, int m1) {
       C* row = sm + g * PS + px * RS;
       C v[N1];
 #pragma unroll
@@ -253,8 +251,38 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
         const int y = m1 + N2 * m2;
         row[y] = apply_delta(C{v[m2].x * scale, v[m2].y * scale}, ldg(qb + y * NX + px));
       }
+    };
+    // Each warp owns LW whole lines when that keeps every half-warp on 16
+    // consecutive lines (conflict-free shared memory): the exchanges between
+    // the passes stay inside the warp, so warps need not wait for one another
+    // until the whole sandwich is done.
+    constexpr int L = G * NX, NW = NT / 32, LW = (L % NW == 0) ? L / NW : 0;
+    constexpr bool WARP_LINES = LW >= 16 && (LW * N2) % 32 == 0 && (LW * N1) % 32 == 0;
+    if constexpr (WARP_LINES) {
+      const int l0 = (tid >> 5) * LW, lane = tid & 31;
+      for (int q = lane; q < LW * N2; q += 32) {
+        const int l = l0 + q % LW;
+        pass1(l / NX, l % NX, q / LW);
+      }
+      __syncwarp();
+      for (int q = lane; q < LW * N1; q += 32) {
+        const int l = l0 + q % LW;
+        pass2(l / NX, l % NX, q / LW);
+      }
+      __syncwarp();
+      for (int q = lane; q < LW * N2; q += 32) {
+        const int l = l0 + q % LW;
+        pass3(l / NX, l % NX, q / LW);
+      }
+      __syncthreads();
+    } else {
+      for (int it = tid; it < G * NX * N2; it += NT) pass1(it / (NX * N2), it % NX, (it / NX) % N2);
+      __syncthreads();
+      for (int it = tid; it < G * NX * N1; it += NT) pass2(it / (NX * N1), it % NX, (it / NX) % N1);
+      __syncthreads();
+      for (int it = tid; it < G * NX * N2; it += NT) pass3(it / (NX * N2), it % NX, (it / NX) % N2);
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
