@@ -7,14 +7,18 @@
  * arXiv:1903.02581: Sec. II.C (two-particle Hamiltonian in the Landau gauge,
  * Eq. evoloperat, parallel 2D Fourier transforms), Appendix A (regrouping of
  * the magnetic kinetic term, Eq. 2PTB), Eq. coulomb (softened interaction),
- * Eq. twopstate (Slater determinant), Eq. singlepwp (edge-state packets) and
- * Eq. p_bunching (bunching probability).
+ * Eq. twopstate (Slater determinant), Eq. singlepwp and Eq. H_effective
+ * (edge-state packets), Eqs. pot_x / pot_xy (barriers), Eq. screenedCoulomb,
+ * Eq. p_bunching (bunching probability), the probability maps of Figs. 2 and
+ * 3(b) and the spatial entanglement of Sec. V.
  *
  * Conventions (units hbar = m* = |e| = 1).  Axes are relabelled with respect
  * to the paper: propagation runs along x, the edge confinement along y.
  *   H_i  = 1/2 (p_x - B y_i)^2 + 1/2 p_y^2 + V1(x_i, y_i)
  *   V1   = 1/2 omega_y^2 y^2 + qpc_h exp(-(x - qpc_x0)^2 / (2 qpc_w^2))
+ *          [+ the Fermi-function blocks of hom_params.fermi_*]
  *   V12  = coul_lambda / sqrt((x1-x2)^2 + (y1-y2)^2 + coul_soft^2)
+ *          [* exp(-|r1 - r2| / coul_screen) when coul_screen > 0]
  *   grid x_j = (j - (nx-1)/2) dx (cell-centred, same for y), k_m = 2 pi m /
  *   (n d) with m in [-n/2, n/2); periodic box; plain coordinate differences.
  *   One step S(dt) = e^{-iV dt/2} F_x^-1 e^{-iT_x dt/2} F_y^-1 e^{-iT_y dt}
@@ -119,9 +123,9 @@ typedef struct hom_ctx hom_ctx;
  * 0 for invalid parameters. */
 size_t hom_state_bytes(const hom_params* p);
 
-/* Bytes of device workspace hom_create needs: one state-sized buffer (each
- * Strang step writes the transposed state psi[b][r2][r1] there between its two
- * passes, so that both passes read contiguous planes), the phase tables,
+/* Bytes of device workspace hom_create needs: one state-sized buffer (the
+ * state alternates between it, as psi[b][r2][r1], and the caller's buffer, so
+ * that each particle's kinetic pass reads contiguous planes), the phase tables,
  * reduction partials, packet buffers and ckpt_slots checkpoints (plus one
  * adjoint state when ckpt_slots > 0).  Returns 0 for invalid parameters. */
 size_t hom_workspace_bytes(const hom_params* p);
