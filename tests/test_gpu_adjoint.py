@@ -127,3 +127,33 @@ def test_autograd_function():
     assert abs(h.grad.item() - 3 * ref["h"]) <= 1e-9 * max(abs(ref["h"]), 1e-2)
     assert abs(wd.grad.item() - 3 * ref["w"]) <= 1e-9 * max(abs(ref["w"]), 1e-2)
     assert abs(d.grad.item() - 3 * ref["delay"]) <= 1e-9 * max(abs(ref["delay"]), 1e-2)
+
+
+def test_adjoint_with_screening_barriers_and_numeric_packets():
+    """The adjoint composes with the potential-family options: screened
+    Coulomb, barrier blocks added to V1 and numerical edge-state packets (with
+    a wall); it still matches the oracle's adjoint and central differences."""
+    nsteps, K = 8, 4
+    w = grad_w("c128")
+    w.update(screen=0.9, fermi_vb=1.5, fermi_tau=0.5, fermi_xa=-2.5, fermi_ya=-2.0, fermi_xb=2.5, fermi_yb=2.0)
+    s = w["sims"][0]
+    s["alpha"] = dict(W.packet(-2.0, 1.0, k0=1.4, by_k0=True), numeric=True, wall_y=-2.5, wall_side=1)
+    s["beta"] = dict(W.packet(2.0, 1.0, k0=-1.4, by_k0=True), numeric=True, wall_y=2.5, wall_side=-1)
+    pr = H().Propagator(w, ckpt_slots=2)
+    loss, grad = pr.backward(nsteps, K)
+    m, a, b = A.packets(w, s)
+    psi0 = O.two_particle(a, b, s["exch"], m.dV)
+    # d psi0 / d(beta centre): the packet is a sum of plane waves in x, so the
+    # derivative is the same sum with weights -i k
+    x = O.coords(m.nx, m.dx)
+    k = O.wavenumbers(m.nx, m.dx)
+    wk = np.exp(-(s["beta"]["sigma"] ** 2) * (k - s["beta"]["k0"]) ** 2)
+    chi = np.array([O.edge_state_numeric(m, float(kk), s["beta"]["wall_y"], s["beta"]["wall_side"])[1]
+                    if wk[i] >= 1e-300 else np.zeros(m.ny) for i, kk in enumerate(k)])
+    plane = np.exp(1j * np.outer(x - s["beta"]["x0"], k))
+    raw = plane @ (wk[:, None] * chi)
+    db = (plane @ ((-1j * k * wk)[:, None] * chi)) / np.sqrt(np.sum(np.abs(raw) ** 2) * m.dx * m.dy)
+    ref_loss, ref = O.loss_and_gradient(psi0, O.slater_dstate(a, b, db, s["exch"], m.dV), m, nsteps)
+    assert abs(loss[0] - ref_loss) <= 1e-12
+    for i, key in enumerate(("h", "w", "delay")):
+        assert abs(grad[0, i] - ref[key]) <= 1e-9 * max(abs(ref[key]), 1e-2), (key, grad[0, i], ref[key])
