@@ -435,7 +435,11 @@ def gb300_arm(args):
         roofline = {"bound": "hbm", "achieved": dom["hbm_gbs"], "peak": peak, "unit": "GB/s",
                     "frac": dom["hbm_frac"], "peak_source": peak_kind}
     step_ms = sum(k[1] for k in kinds) / max(args.steps * args.inner, 1)
-    roofline.update({"traffic": ncu_traffic(name) if args.workload == "fullscale" else None,
+    traffic = ncu_traffic(name) if args.workload == "fullscale" else None
+    roofline.update({"traffic": traffic,
+                     # HBM fraction from the measured DRAM bytes of one ncu capture
+                     # over the live average launch time
+                     "hbm_frac_ncu_bytes": (traffic / (dom["avg_ms"] / 1000.0) / 1e9 / peak) if traffic else None,
                      "kernel": name, "kernels": per_kernel,
                      "hbm_peak_gbs": peak,
                      # the two-round-trip floor: 32 B per point per step (complex64)
