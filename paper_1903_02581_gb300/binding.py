@@ -8,6 +8,7 @@ if the library is missing, ``lib()`` raises.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import re
@@ -305,50 +306,77 @@ class Propagator:
         self.device = torch.device(device)
         self.state = torch.empty((self.batch, n, n), dtype=self.dtype, device=self.device)
         self.workspace = torch.empty(wb, dtype=torch.uint8, device=self.device)
-        # A stream of its own (blocking, so that work on torch's default stream
-        # stays ordered with it): hom_step captures its launches into CUDA
-        # graphs, which the legacy default stream cannot hold.
+        # A stream of its own: hom_step captures its launches into CUDA graphs,
+        # which the legacy default stream cannot hold.  Streams from torch's
+        # pool do not synchronise with the default stream, so every call below
+        # runs between two cross-stream waits (_ordered): the library sees what
+        # torch wrote to the state before the call, and torch work issued after
+        # it sees what the library wrote.
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
         self.state.record_stream(self.stream)
         self.workspace.record_stream(self.stream)
-        self.ctx = hom_create(self.params, self.state.data_ptr(), self.workspace.data_ptr(), wb,
-                              self.stream.cuda_stream)
-        if "sims" in w:
-            for b, s in enumerate(w["sims"]):
-                hom_set_sim_params(self.ctx, b, s["qpc_h"], s["qpc_w"], s["lam"])
-                if init:
-                    hom_init_packets(self.ctx, b, make_packet(s["alpha"]), make_packet(s["beta"]), s["exch"])
+        with self._ordered():
+            self.ctx = hom_create(self.params, self.state.data_ptr(), self.workspace.data_ptr(), wb,
+                                  self.stream.cuda_stream)
+            if "sims" in w:
+                for b, s in enumerate(w["sims"]):
+                    hom_set_sim_params(self.ctx, b, s["qpc_h"], s["qpc_w"], s["lam"])
+                    if init:
+                        hom_init_packets(self.ctx, b, make_packet(s["alpha"]), make_packet(s["beta"]),
+                                         s["exch"])
+
+    @contextlib.contextmanager
+    def _ordered(self):
+        import torch
+
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream == self.stream.cuda_stream:
+            yield
+            return
+        self.stream.wait_stream(cur)
+        try:
+            yield
+        finally:
+            cur.wait_stream(self.stream)
 
     def step(self, nsteps: int):
-        hom_step(self.ctx, nsteps)
+        with self._ordered():
+            hom_step(self.ctx, nsteps)
 
     def observables(self) -> list[dict]:
-        return hom_observables(self.ctx, self.batch)
+        with self._ordered():
+            return hom_observables(self.ctx, self.batch)
 
     def backward(self, nsteps: int, K: int):
-        return hom_backward(self.ctx, self.batch, nsteps, K)
+        with self._ordered():
+            return hom_backward(self.ctx, self.batch, nsteps, K)
 
     def marginal(self) -> np.ndarray:
         """Unconditional probability density of particle 1, [batch][nx][ny]."""
-        return hom_marginal(self.ctx, self.batch, self.w["nx"], self.w["ny"])
+        with self._ordered():
+            return hom_marginal(self.ctx, self.batch, self.w["nx"], self.w["ny"])
 
     def conditional(self, b: int, ix2: int, iy2: int) -> np.ndarray:
         """|psi(x1, y1, x2*, y2*)|^2 of simulation b, [nx][ny]."""
-        return hom_conditional(self.ctx, b, ix2, iy2, self.w["nx"], self.w["ny"])
+        with self._ordered():
+            return hom_conditional(self.ctx, b, ix2, iy2, self.w["nx"], self.w["ny"])
 
     def entanglement(self, b: int, iy1: int, iy2: int, x1_range, x2_range) -> tuple[float, float]:
         """(von Neumann entropy, slice weight) of the slice at (y1*, y2*)."""
-        return hom_entanglement(self.ctx, b, iy1, iy2, x1_range, x2_range)
+        with self._ordered():
+            return hom_entanglement(self.ctx, b, iy1, iy2, x1_range, x2_range)
 
     def get_state(self, b: int = 0) -> np.ndarray:
         nx, ny = self.w["nx"], self.w["ny"]
         out = np.empty((nx, ny, nx, ny), dtype=self.np_dtype)
-        hom_copy_state(self.ctx, b, out, to_device=False)
+        with self._ordered():
+            hom_copy_state(self.ctx, b, out, to_device=False)
         return out
 
     def set_state(self, b: int, arr: np.ndarray):
         a = np.ascontiguousarray(arr, dtype=self.np_dtype)
-        hom_copy_state(self.ctx, b, a, to_device=True)
+        with self._ordered():
+            hom_copy_state(self.ctx, b, a, to_device=True)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -222,6 +222,36 @@ def test_fullscale_zero_coulomb_rows_match_factorised_oracle(full_zero_coulomb):
     assert worst <= TOL["c64"], worst
 
 
+def test_c128_maximum_plane_zero_coulomb_rows_match_factorised_oracle():
+    """complex128 at its largest plane (128 x 64 per electron, nx*ny = 8192,
+    a 1 GiB state): with lam = 0 the evolved state is the antisymmetrised
+    product of the two single-particle evolutions, so sampled rows are checked
+    against the FP64 2D oracle at the FP64 tolerance."""
+    w = W.shrink(W.fullscale(sigma=2.0), nx=128)
+    w["prec"] = "c128"
+    w["sims"][0]["lam"] = 0.0
+    nsteps = 20
+    pr = H().Propagator(w)
+    pr.step(nsteps)
+    m, a, b = A.packets(w, w["sims"][0])
+    a_f = O.propagate_2d(a, m, nsteps).ravel()
+    b_f = O.propagate_2d(b, m, nsteps).ravel()
+    ab = np.vdot(a_f, b_f) * m.dx * m.dy
+    c = 1.0 / math.sqrt(2.0 * (1.0 - abs(ab) ** 2))
+    l2 = 1.0 / math.sqrt(m.dV)
+    n = w["nx"] * w["ny"]
+    rows = np.random.default_rng(W.SEED + 1).choice(n, size=12, replace=False)
+    worst = 0.0
+    for r1 in rows:
+        got = pr.state[0, int(r1), :].cpu().numpy()
+        ref = c * (a_f[r1] * b_f - b_f[r1] * a_f)
+        worst = max(worst, float(np.max(np.abs(got - ref))) / l2)
+    assert worst <= TOL["c128"], worst
+    o = pr.observables()[0]
+    assert abs(o["norm"] - 1.0) < 1e-10
+    pr.close()
+
+
 def test_fullscale_invariants_with_coulomb():
     import torch
 
