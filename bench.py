@@ -12,10 +12,12 @@ of the observables (norm, energy terms, bunching probability).
            time), inputs resident in HBM, max time over ranks;
   e2e    = the same metric through the C ABI with the state copied from
            pinned host memory every step and the observables read back;
-  roofline = the dominant kernel's algorithmic bytes (16 B per point per pass
-           in complex64: one read, one write) over its average CUDA-event
-           duration, against the measured HBM copy bandwidth;
-  cpu_baseline = the FP64 oracle on the machine's host cores on a bounded sample.
+  roofline = the dominant kernel's algorithmic work over its average
+           CUDA-event duration: bytes (16 B per point per pass in complex64:
+           one read, one write) against the measured HBM copy bandwidth, and
+           FP32 flops against the FP32 peak of the SM count and clock; the
+           line reports whichever fraction is higher as the bound;
+  cpu_baseline = the FP64 oracle on the host cores on a bounded sample.
 
 Multi-GPU: one process per GPU (torchrun); each rank propagates its own
 simulation (weak scaling), no collective on the data path.
