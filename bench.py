@@ -337,7 +337,6 @@ def reference_arm(args):
 
 
 def gb300_arm(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -350,7 +349,7 @@ def gb300_arm(args):
 
     from paper_1903_02581_gb300 import binding as H
     from paper_1903_02581_gb300 import build as Bd
-    from paper_1903_02581_gb300 import workloads as W
+    from paper_1903_02581_gb300 import replicas as RP
 
     if rank == 0:
         Bd.build()
@@ -358,13 +357,7 @@ def gb300_arm(args):
         dist.barrier()
     H.lib()
 
-    if args.workload == "batched":
-        w = W.batched()
-        wname = "batched-32x128x32"
-    else:
-        sigma = [2.0, 1.0, 4.0][rank % 3]
-        w = W.fullscale(sigma=sigma)
-        wname = "fullscale-256x64"
+    w, wname = RP.rank_workload(args.workload, rank)
     pts = (w["nx"] * w["ny"]) ** 2
     batch = len(w["sims"])
     pr = H.Propagator(w, device=f"cuda:{local}")
@@ -400,12 +393,8 @@ def gb300_arm(args):
     tuning = H.hom_autotune_info(pr.ctx)
     H.hom_profile(pr.ctx, False)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * batch * pts * args.inner * args.steps / (ms_max / 1000.0)
+    ms_max = RP.slowest(ev0.elapsed_time(ev1), device=f"cuda:{local}")
+    value = RP.job_rate(world, batch, pts, args.inner * args.steps, ms_max / 1000.0)
 
     # dominant kernel and its roofline.  Algorithmic bytes: one read and one
     # write of the state per launch.  Algorithmic FP32 flops: one kinetic
@@ -470,11 +459,8 @@ def gb300_arm(args):
             pr.observables()                                               # synchronises
             reps.append([round((tb - ta) * 1e3, 2), round((time.perf_counter() - tb) * 1e3, 2)])
         torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        sec_t = torch.tensor([sec], dtype=torch.float64, device=f"cuda:{local}")
-        if world > 1:
-            dist.all_reduce(sec_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * batch * pts * args.inner * nrep / float(sec_t.item()), "unit": "updates/s",
+        sec = RP.slowest(time.perf_counter() - t0, device=f"cuda:{local}")
+        e2e = {"value": RP.job_rate(world, batch, pts, args.inner * nrep, sec), "unit": "updates/s",
                "h2d_bytes_per_step": int(hview.nbytes), "d2h_bytes_per_step": 48 * batch, "steps": nrep,
                "ms_copy_and_steps_per_rep": reps}
 

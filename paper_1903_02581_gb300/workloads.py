@@ -81,9 +81,14 @@ def gradient():
     return p
 
 
-def batched(nsim=32):
-    """nsim x 128x32 per electron (16,777,216 points each, complex64), dt=0.004, 1500 steps."""
-    rng = np.random.default_rng(SEED + 5)
+def batched(nsim=32, shard=0):
+    """nsim x 128x32 per electron (16,777,216 points each, complex64), dt=0.004, 1500 steps.
+
+    ``shard`` selects one block of nsim simulations of a larger sweep (one
+    block per process when the sweep is spread over several GPUs): shard 0 is
+    this sweep itself, and every other shard draws its delays and widths from
+    a stream of its own."""
+    rng = np.random.default_rng(SEED + 5 if shard == 0 else [SEED + 5, int(shard)])
     p = _base(128, 32, 0.5, 0.5, dt=0.004, nsteps=1500, prec="c64", soft=0.5)
     delay = rng.uniform(-4.0, 4.0, size=nsim)
     sigma = rng.uniform(1.0, 3.0, size=nsim)
