@@ -5,7 +5,8 @@ Workload (default): the full-scale configuration, 256x64 grid per electron
 dt = 0.002, Coulomb strength 1 (softening 0.25), QPC height 1 / width 2,
 packets of energy 3 started at x = -24 / +24.  One bench "step" is one pass
 of the hot path at the workload's observation cadence: 100 Strang steps
-(two kinetic passes each, potential phase fused) followed by one evaluation
+(two HBM round trips each: the autotuner's launch sequence of kinetic passes
+and transposes, potential phase fused) followed by one evaluation
 of the observables (norm, energy terms, bunching probability).
 
   value  = whole-job grid-point updates per second (points x Strang steps /

@@ -223,7 +223,8 @@ struct hom_ctx {
   bool use_graphs;
   // autotuner: kernel variant of the transposing [0] and in-place [1] passes,
   // and the step strategy (0: transposing pass + in-place pass; 1: in-place
-  // pass + transpose + in-place pass)
+  // pass + transpose + in-place pass; 2: one double in-place pass + transpose
+  // per step, see step_sequence)
   int variant[2];
   int strategy;
   bool tuned;
