@@ -1,5 +1,5 @@
-"""Exchange symmetry of the whole propagation on the GPU (complex128), with
-Coulomb repulsion, through a full scattering event at the saddle.
+"""Exchange symmetry and the Hong-Ou-Mandel dip of the whole propagation on
+the GPU, through a full scattering event at the saddle.
 
 The Hamiltonian and the bunching mask are symmetric under the swap of the
 particles, so for the antisymmetrised (-), symmetrised (+) and product
@@ -9,15 +9,20 @@ states built from the same two normalised packets (Eq. twopstate),
 
 at every time, P being the bunching probability (Eq. p_bunching) of each
 renormalised state.  A kernel that treated the two particles differently, or
-an exchange sign applied wrongly, breaks it.  Without interaction the
-antisymmetric state also shows the Hong-Ou-Mandel dip and the symmetric one
-the peak (Sec. IV): at zero delay P_- is below, and P_+ above, their values
-at a delay where the packets barely overlap.
+an exchange sign applied wrongly, breaks it.  Checked in complex128 on a
+64 x 32 grid per electron, with and without Coulomb, at two delays.
 
-Grid 64 x 32 per electron (dx = dy = 0.5: a 32 x 16 box), packets of width
-1.5 and energy 2.5 from x = -3 and x = 3 + delay, a saddle of height 2.25
-(about half of a single packet is transmitted), run to t = 10, after both
-packets have passed the saddle."""
+Without interaction the antisymmetric state shows the Hong-Ou-Mandel dip and
+the symmetric one the peak (Sec. IV), and a sweep of the delay follows the
+1D scattering model of Eq. bunching, which the paper fits to its own
+simulations.  Those runs use a 256 x 32 grid (dx = dy = 0.5: a 128 x 16 box)
+in complex64, packets of width 1.5 and energy 2.5 started at
+x = -(15 - delay/2) and 15 + delay/2 (beta travels `delay` further; both
+start at least 11 away from the saddle, which has width 1.5, so that the
+delay changes only the arrival times: a single packet is transmitted with
+probability 0.5093 from every start used), a saddle of height 1.85, and stop
+at t = 28, when the packets have left the saddle and none has come near the
+periodic edge."""
 
 import numpy as np
 import pytest
@@ -27,11 +32,8 @@ from paper_1903_02581_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-T_END, DT = 10.0, 0.01
 
-
-@pytest.fixture(scope="module")
-def runs():
+def _binding():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -39,47 +41,90 @@ def runs():
     from paper_1903_02581_gb300 import build
 
     build.build()
-    w = W.sweep32(prec="c128")
-    w.update(nx=64, ny=32, dx=0.5, dy=0.5, dt=DT)
+    return H
 
-    def sim(lam, delay, exch):
+
+def _run(w, keys, make):
+    H = _binding()
+    w["sims"] = [make(*k) for k in keys]
+    w["batch"] = len(keys)
+    pr = H.Propagator(w)
+    pr.step(round(w["t_end"] / w["dt"]))
+    obs = pr.observables()
+    pr.close()
+    return w, obs
+
+
+@pytest.fixture(scope="module")
+def identity_runs():
+    w = W.sweep32(prec="c128")
+    w.update(nx=64, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=9.0)
+
+    def make(lam, delay, exch):
         return dict(qpc_h=2.25, qpc_w=1.5, lam=lam, exch=exch,
                     alpha=W.packet(-3.0, 1.5, 2.5, +1), beta=W.packet(3.0 + delay, 1.5, 2.5, -1))
 
-    keys = [(lam, delay, exch) for lam, delay in ((1.0, 0.0), (1.0, 4.0), (0.0, 0.0), (0.0, 6.0))
-            for exch in (-1, 0, 1)]
-    w["sims"] = [sim(*k) for k in keys]
-    w["batch"] = len(keys)
-    pr = H.Propagator(w)
-    pr.step(round(T_END / DT))
-    obs = pr.observables()
-    pr.close()
+    keys = [(lam, delay, exch) for lam in (1.0, 0.0) for delay in (0.0, 4.0) for exch in (-1, 0, 1)]
+    w, obs = _run(w, keys, make)
     out = {}
     for k, o, s in zip(keys, obs, w["sims"]):
         assert abs(o["norm"] - 1.0) < 1e-11
         m, a, b = A.packets(w, s)
-        ov = np.vdot(a.ravel(), b.ravel()) * m.dx * m.dy
-        out[k] = (o["p_bunch"], abs(ov) ** 2)
+        out[k] = (o["p_bunch"], abs(np.vdot(a.ravel(), b.ravel()) * m.dx * m.dy) ** 2)
     return out
 
 
-@pytest.mark.parametrize("lam,delay", [(1.0, 0.0), (1.0, 4.0), (0.0, 0.0), (0.0, 6.0)])
-def test_exchange_sum_identity(runs, lam, delay):
-    pm, s2 = runs[(lam, delay, -1)]
-    p0, _ = runs[(lam, delay, 0)]
-    pp, _ = runs[(lam, delay, 1)]
+@pytest.mark.parametrize("lam,delay", [(1.0, 0.0), (1.0, 4.0), (0.0, 0.0), (0.0, 4.0)])
+def test_exchange_sum_identity(identity_runs, lam, delay):
+    pm, s2 = identity_runs[(lam, delay, -1)]
+    p0, _ = identity_runs[(lam, delay, 0)]
+    pp, _ = identity_runs[(lam, delay, 1)]
     assert abs((1 + s2) * pp + (1 - s2) * pm - 2 * p0) <= 1e-11, (pm, p0, pp, s2)
 
 
-def test_hong_ou_mandel_dip_and_peak(runs):
-    anti0, sym0 = runs[(0.0, 0.0, -1)][0], runs[(0.0, 0.0, 1)][0]
-    antid, symd = runs[(0.0, 6.0, -1)][0], runs[(0.0, 6.0, 1)][0]
-    prod = runs[(0.0, 0.0, 0)][0]
-    print("P_b: antisymmetric", anti0, antid, "symmetric", sym0, symd, "product", prod)
-    assert 0.1 < prod < 0.9                        # the saddle splits the packets
-    # The saddle's transmission varies over the energy spread of these narrow
-    # packets (the parameter a of Eq. bunching), so the dip and the peak are
-    # shallow; they still exceed FP64 noise by ten orders of magnitude.
+SWEEP = (0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 8.0)
+
+
+@pytest.fixture(scope="module")
+def hom_runs():
+    w = W.sweep32(prec="c64")
+    w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=28.0)
+
+    def make(delay, exch):
+        return dict(qpc_h=1.85, qpc_w=1.5, lam=0.0, exch=exch,
+                    alpha=W.packet(-15.0 + delay / 2, 1.5, 2.5, +1), beta=W.packet(15.0 + delay / 2, 1.5, 2.5, -1))
+
+    keys = [(d, -1) for d in SWEEP] + [(0.0, 1), (8.0, 1), (0.0, 0), (8.0, 0)]
+    _, obs = _run(w, keys, make)
+    return {k: o["p_bunch"] / o["norm"] for k, o in zip(keys, obs)}
+
+
+def test_hong_ou_mandel_dip_and_peak(hom_runs):
+    anti0, sym0, prod0 = hom_runs[(0.0, -1)], hom_runs[(0.0, 1)], hom_runs[(0.0, 0)]
+    antid, symd, prodd = hom_runs[(8.0, -1)], hom_runs[(8.0, 1)], hom_runs[(8.0, 0)]
+    print("P_b: antisymmetric", anti0, antid, "symmetric", sym0, symd, "product", prod0, prodd)
+    assert 0.4 < prod0 < 0.6                       # the saddle splits the packets about evenly
+    assert abs(prod0 - prodd) < 1e-3               # distinguishable: the delay does not matter
     assert anti0 < antid - 0.01                    # dip
     assert sym0 > symd + 0.01                      # peak
-    assert anti0 < prod < sym0
+    assert anti0 < prod0 < sym0
+
+
+def test_delay_sweep_follows_the_1d_model(hom_runs):
+    """The antisymmetric sweep fitted with Eq. bunching, as the paper fits its
+    simulations: the dip fills in monotonically with the delay, the fit
+    leaves residuals of a few percent of the dip depth, and the fitted packet
+    width is within 20 % of the width the packets were built with (1.5; the
+    model's width is the same standard deviation of |psi|^2 along the edge)."""
+    from paper_1903_02581_gb300 import analysis as AN
+
+    d = np.array(SWEEP)
+    pb = np.array([hom_runs[(x, -1)] for x in SWEEP])
+    sigma, a = AN.fit_bunching_1d(d, pb, sigma0=1.5, a0=5.0)
+    fit = AN.bunching_1d(d, sigma, a)
+    depth = 0.5 - pb[0]
+    print("P_b(delay):", pb, "fit sigma, a:", sigma, a, "residuals:", pb - fit)
+    assert np.all(np.diff(pb) > 0)
+    assert depth > 0.03
+    assert np.max(np.abs(pb - fit)) <= 0.05 * depth
+    assert 1.2 < sigma < 1.8
