@@ -15,14 +15,16 @@ an exchange sign applied wrongly, breaks it.  Checked in complex128 on a
 Without interaction the antisymmetric state shows the Hong-Ou-Mandel dip and
 the symmetric one the peak (Sec. IV), and a sweep of the delay follows the
 1D scattering model of Eq. bunching, which the paper fits to its own
-simulations.  Those runs use a 256 x 32 grid (dx = dy = 0.5: a 128 x 16 box)
-in complex64, packets of width 1.5 and energy 2.5 started at
-x = -(15 - delay/2) and 15 + delay/2 (beta travels `delay` further; both
-start at least 11 away from the saddle, which has width 1.5, so that the
-delay changes only the arrival times: a single packet is transmitted with
-probability 0.5093 from every start used), a saddle of height 1.85, and stop
-at t = 28, when the packets have left the saddle and none has come near the
-periodic edge."""
+simulations; wider packets antibunch more, and Coulomb repulsion adds its
+own antibunching (Sec. III).  Those runs use a 256 x 32 grid (dx = dy = 0.5:
+a 128 x 16 box) in complex64, packets of energy 2.5 and width 1.5 (1 to 3
+for the width scan) started at x = -(x_s - delay/2) and x_s + delay/2 (beta
+travels `delay` further; x_s = 15, more for wider packets, so that they start
+clear of the saddle, which has width 1.5, and the delay changes only the
+arrival times: a single packet is transmitted with probability 0.5093 from
+every start used), a saddle of height 1.85, and stop at t = 26, when the
+packets have left the saddle (P_b changes by less than 3e-4 after that) and
+none has come near the periodic edge."""
 
 import numpy as np
 import pytest
@@ -83,25 +85,30 @@ def test_exchange_sum_identity(identity_runs, lam, delay):
 
 
 SWEEP = (0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 8.0)
+SIGMAS = (1.0, 1.5, 2.0, 2.5, 3.0)
 
 
 @pytest.fixture(scope="module")
 def hom_runs():
+    """One batch of 28 simulations, keyed (sigma, delay, exch, lam)."""
     w = W.sweep32(prec="c64")
-    w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=28.0)
+    w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=26.0)
 
-    def make(delay, exch):
-        return dict(qpc_h=1.85, qpc_w=1.5, lam=0.0, exch=exch,
-                    alpha=W.packet(-15.0 + delay / 2, 1.5, 2.5, +1), beta=W.packet(15.0 + delay / 2, 1.5, 2.5, -1))
+    def make(sigma, delay, exch, lam):
+        xs = 15.0 + 3.0 * max(0.0, sigma - 1.5)   # wider packets start further out
+        return dict(qpc_h=1.85, qpc_w=1.5, lam=lam, exch=exch,
+                    alpha=W.packet(-xs + delay / 2, sigma, 2.5, +1), beta=W.packet(xs + delay / 2, sigma, 2.5, -1))
 
-    keys = [(d, -1) for d in SWEEP] + [(0.0, 1), (8.0, 1), (0.0, 0), (8.0, 0)]
+    keys = [(1.5, d, -1, 0.0) for d in SWEEP] + [(1.5, 0.0, 1, 0.0), (1.5, 8.0, 1, 0.0), (1.5, 8.0, 0, 0.0)]
+    keys += [(s, 0.0, 0, 0.0) for s in SIGMAS] + [(s, 0.0, -1, 0.0) for s in SIGMAS if s != 1.5]
+    keys += [(1.5, d, -1, 1.0) for d in SWEEP] + [(1.5, 0.0, 0, 1.0), (1.5, 8.0, 0, 1.0)]
     _, obs = _run(w, keys, make)
     return {k: o["p_bunch"] / o["norm"] for k, o in zip(keys, obs)}
 
 
 def test_hong_ou_mandel_dip_and_peak(hom_runs):
-    anti0, sym0, prod0 = hom_runs[(0.0, -1)], hom_runs[(0.0, 1)], hom_runs[(0.0, 0)]
-    antid, symd, prodd = hom_runs[(8.0, -1)], hom_runs[(8.0, 1)], hom_runs[(8.0, 0)]
+    anti0, sym0, prod0 = hom_runs[(1.5, 0.0, -1, 0.0)], hom_runs[(1.5, 0.0, 1, 0.0)], hom_runs[(1.5, 0.0, 0, 0.0)]
+    antid, symd, prodd = hom_runs[(1.5, 8.0, -1, 0.0)], hom_runs[(1.5, 8.0, 1, 0.0)], hom_runs[(1.5, 8.0, 0, 0.0)]
     print("P_b: antisymmetric", anti0, antid, "symmetric", sym0, symd, "product", prod0, prodd)
     assert 0.4 < prod0 < 0.6                       # the saddle splits the packets about evenly
     assert abs(prod0 - prodd) < 1e-3               # distinguishable: the delay does not matter
@@ -119,7 +126,7 @@ def test_delay_sweep_follows_the_1d_model(hom_runs):
     from paper_1903_02581_gb300 import analysis as AN
 
     d = np.array(SWEEP)
-    pb = np.array([hom_runs[(x, -1)] for x in SWEEP])
+    pb = np.array([hom_runs[(1.5, x, -1, 0.0)] for x in SWEEP])
     sigma, a = AN.fit_bunching_1d(d, pb, sigma0=1.5, a0=5.0)
     fit = AN.bunching_1d(d, sigma, a)
     depth = 0.5 - pb[0]
@@ -128,3 +135,42 @@ def test_delay_sweep_follows_the_1d_model(hom_runs):
     assert depth > 0.03
     assert np.max(np.abs(pb - fit)) <= 0.05 * depth
     assert 1.2 < sigma < 1.8
+
+
+def test_bunching_falls_with_packet_width(hom_runs):
+    """Sec. III(A): without interaction the antisymmetric state's stationary
+    P_b decreases about linearly as the packets get wider (full antibunching
+    is the plane-wave limit), while the product state stays at the classical
+    value 2 T (1 - T), here 1/2."""
+    anti = np.array([hom_runs[(s, 0.0, -1, 0.0)] for s in SIGMAS])
+    prod = np.array([hom_runs[(s, 0.0, 0, 0.0)] for s in SIGMAS])
+    print("P_b(sigma): antisymmetric", anti, "product", prod)
+    assert np.all(np.abs(prod - 0.5) < 2e-3)
+    slope = np.diff(anti)
+    assert np.all(slope < -0.02)
+    assert np.max(np.abs(np.diff(slope))) < 0.25 * np.mean(np.abs(slope))
+
+
+def test_coulomb_antibunching_and_effective_parameters(hom_runs):
+    """Sec. III(B): Coulomb repulsion alone antibunches a product state (P_b
+    below 1/2, less so when the delay keeps the packets apart, and not down to
+    0 in 2D); with exchange as well, P_b is shifted lower still; and a fit of
+    Eq. bunching to the interacting delay sweep needs an effective width and
+    range larger than the non-interacting ones."""
+    from paper_1903_02581_gb300 import analysis as AN
+
+    prod0, prodd = hom_runs[(1.5, 0.0, 0, 1.0)], hom_runs[(1.5, 8.0, 0, 1.0)]
+    anti0 = hom_runs[(1.5, 0.0, -1, 1.0)]
+    free_anti0 = hom_runs[(1.5, 0.0, -1, 0.0)]
+    print("Coulomb: product", prod0, prodd, "antisymmetric", anti0, "(no Coulomb", free_anti0, ")")
+    assert 0.1 < prod0 < prodd < 0.5 - 0.02
+    assert anti0 < prod0 and anti0 < free_anti0
+    d = np.array(SWEEP)
+    pb_int = np.array([hom_runs[(1.5, x, -1, 1.0)] for x in SWEEP])
+    pb_free = np.array([hom_runs[(1.5, x, -1, 0.0)] for x in SWEEP])
+    assert np.all(np.diff(pb_int) > 0)
+    s_int, a_int = AN.fit_bunching_1d(d, pb_int, sigma0=1.5, a0=10.0)
+    s_free, a_free = AN.fit_bunching_1d(d, pb_free, sigma0=1.5, a0=10.0)
+    print("fits: interacting", s_int, a_int, "free", s_free, a_free)
+    assert np.max(np.abs(pb_int - AN.bunching_1d(d, s_int, a_int))) <= 0.05 * (0.5 - pb_int[0])
+    assert s_int > 1.3 * s_free and a_int > a_free
