@@ -174,3 +174,20 @@ def test_coulomb_antibunching_and_effective_parameters(hom_runs):
     print("fits: interacting", s_int, a_int, "free", s_free, a_free)
     assert np.max(np.abs(pb_int - AN.bunching_1d(d, s_int, a_int))) <= 0.05 * (0.5 - pb_int[0])
     assert s_int > 1.3 * s_free and a_int > a_free
+
+
+def test_screening_restores_exchange_driven_bunching(hom_runs):
+    """Sec. III(B), Eq. screenedCoulomb: damping the repulsion over a range
+    sigma_c brings the interacting antisymmetric P_b back towards its value
+    without interaction, the more so the shorter the range."""
+    w = W.sweep32(prec="c64")
+    w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=26.0)
+    make = lambda: dict(qpc_h=1.85, qpc_w=1.5, lam=1.0, exch=-1,  # noqa: E731
+                        alpha=W.packet(-15.0, 1.5, 2.5, +1), beta=W.packet(15.0, 1.5, 2.5, -1))
+    screened = {}
+    for sc in (3.0, 1.0):
+        _, obs = _run(dict(w, screen=sc), [()], make)
+        screened[sc] = obs[0]["p_bunch"] / obs[0]["norm"]
+    free, full = hom_runs[(1.5, 0.0, -1, 0.0)], hom_runs[(1.5, 0.0, -1, 1.0)]
+    print("P_b: free", free, "screened 1.0", screened[1.0], "screened 3.0", screened[3.0], "unscreened", full)
+    assert abs(screened[1.0] - free) < abs(screened[3.0] - free) < abs(full - free)
