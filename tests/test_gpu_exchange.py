@@ -15,8 +15,9 @@ an exchange sign applied wrongly, breaks it.  Checked in complex128 on a
 Without interaction the antisymmetric state shows the Hong-Ou-Mandel dip and
 the symmetric one the peak (Sec. IV), and a sweep of the delay follows the
 1D scattering model of Eq. bunching, which the paper fits to its own
-simulations; wider packets antibunch more, and Coulomb repulsion adds its
-own antibunching (Sec. III).  Those runs use a 256 x 32 grid (dx = dy = 0.5:
+simulations; wider packets antibunch more, Coulomb repulsion adds its own
+antibunching (Sec. III), and the entanglement between the output arms
+follows the trends of Sec. V.  Those runs use a 256 x 32 grid (dx = dy = 0.5:
 a 128 x 16 box) in complex64, packets of energy 2.5 and width 1.5 (1 to 3
 for the width scan) started at x = -(x_s - delay/2) and x_s + delay/2 (beta
 travels `delay` further; x_s = 15, more for wider packets, so that they start
@@ -46,15 +47,26 @@ def _binding():
     return H
 
 
-def _run(w, keys, make):
+def _run(w, keys, make, extra=None):
     H = _binding()
     w["sims"] = [make(*k) for k in keys]
     w["batch"] = len(keys)
     pr = H.Propagator(w)
     pr.step(round(w["t_end"] / w["dt"]))
     obs = pr.observables()
+    if extra is not None:
+        for b, o in enumerate(obs):
+            o.update(extra(pr, b))
     pr.close()
     return w, obs
+
+
+def _arm_entropy(pr, b):
+    """Von Neumann entropy (Sec. V) of the slice that joins the two output
+    arms: x1 > 0 on the right-moving edge (y1 = +1.25) and x2 < 0 on the
+    left-moving edge (y2 = -1.25), for the 256 x 32 grid below."""
+    s, weight = pr.entanglement(b, 18, 13, (128, 256), (0, 128))
+    return {"entropy": s, "arm_weight": weight}
 
 
 @pytest.fixture(scope="module")
@@ -102,8 +114,12 @@ def hom_runs():
     keys = [(1.5, d, -1, 0.0) for d in SWEEP] + [(1.5, 0.0, 1, 0.0), (1.5, 8.0, 1, 0.0), (1.5, 8.0, 0, 0.0)]
     keys += [(s, 0.0, 0, 0.0) for s in SIGMAS] + [(s, 0.0, -1, 0.0) for s in SIGMAS if s != 1.5]
     keys += [(1.5, d, -1, 1.0) for d in SWEEP] + [(1.5, 0.0, 0, 1.0), (1.5, 8.0, 0, 1.0)]
-    _, obs = _run(w, keys, make)
+    _, obs = _run(w, keys, make, extra=_arm_entropy)
+    entropy.update({k: o["entropy"] for k, o in zip(keys, obs)})
     return {k: o["p_bunch"] / o["norm"] for k, o in zip(keys, obs)}
+
+
+entropy = {}   # filled by hom_runs: (sigma, delay, exch, lam) -> entropy of the output-arm slice
 
 
 def test_hong_ou_mandel_dip_and_peak(hom_runs):
@@ -191,3 +207,19 @@ def test_screening_restores_exchange_driven_bunching(hom_runs):
     free, full = hom_runs[(1.5, 0.0, -1, 0.0)], hom_runs[(1.5, 0.0, -1, 1.0)]
     print("P_b: free", free, "screened 1.0", screened[1.0], "screened 3.0", screened[3.0], "unscreened", full)
     assert abs(screened[1.0] - free) < abs(screened[3.0] - free) < abs(full - free)
+
+
+def test_output_arm_entanglement(hom_runs):
+    """Sec. V: the spatial entanglement between the two output arms, from the
+    slice that joins them.  A product state without interaction has none;
+    with exchange alone it falls as the packets get wider (it vanishes in the
+    plane-wave limit); Coulomb repulsion quenches the antisymmetric state's
+    entanglement, and entangles a product state on its own."""
+    S = entropy
+    anti = np.array([S[(s, 0.0, -1, 0.0)] for s in SIGMAS])
+    print("S: antisymmetric by sigma", anti, "product", S[(1.5, 0.0, 0, 0.0)], "with Coulomb: antisymmetric",
+          S[(1.5, 0.0, -1, 1.0)], "product", S[(1.5, 0.0, 0, 1.0)])
+    assert S[(1.5, 0.0, 0, 0.0)] < 1e-5
+    assert np.all(np.diff(anti) < -0.02)
+    assert S[(1.5, 0.0, -1, 1.0)] < 0.7 * S[(1.5, 0.0, -1, 0.0)]
+    assert S[(1.5, 0.0, 0, 1.0)] > 0.05
