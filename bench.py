@@ -17,7 +17,10 @@ of the observables (norm, energy terms, bunching probability).
            CUDA-event duration: bytes (16 B per point per pass in complex64:
            one read, one write) against the measured HBM copy bandwidth, and
            FP32 flops against the FP32 peak of the SM count and clock; the
-           line reports whichever fraction is higher as the bound;
+           line reports whichever fraction is higher as the bound; its
+           traffic (DRAM bytes) and ncu_pipes (FMA pipe, issue, L1 data
+           pipe and DRAM utilisation) come from the committed ncu summary of
+           the same kernel sources, and are null for any other sources;
   cpu_baseline = the FP64 oracle on the host cores on a bounded sample.
 
 Multi-GPU: one process per GPU (torchrun); each rank propagates its own
@@ -147,12 +150,12 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
-    None when the summary was taken on different kernel sources."""
+def _ncu_summary() -> dict:
+    """Key/value lines of the committed ncu summary, or {} when it is absent
+    or was taken on different kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     with open(path) as f:
         for line in f:
@@ -160,9 +163,25 @@ def ncu_traffic(kernel: str):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("kernel_sources_sha256_16") != kernel_hash():
-        return None
-    v = vals.get(f"{kernel}_dram_bytes_per_launch_full_scale")
+        return {}
+    return vals
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when the summary was taken on different kernel sources."""
+    v = _ncu_summary().get(f"{kernel}_dram_bytes_per_launch_full_scale")
     return float(v) if v else None
+
+
+def ncu_pipes(kernel: str):
+    """Pipe utilisation of ``kernel`` (fractions of ncu's peaks) from the same
+    summary: FMA pipe, instruction issue, L1 data pipe, DRAM; None when absent."""
+    vals = _ncu_summary()
+    keys = {"fma_pipe": "fma_pipe_active", "issue": "issue_active",
+            "l1_data_pipe": "l1_data_pipe_wavefronts", "dram": "dram_throughput"}
+    out = {k: float(vals[f"{kernel}_{v}"]) for k, v in keys.items() if f"{kernel}_{v}" in vals}
+    return out or None
 
 
 class ClockSampler:
@@ -429,6 +448,9 @@ def gb300_arm(args):
     step_ms = sum(k[1] for k in kinds) / max(args.steps * args.inner, 1)
     traffic = ncu_traffic(name) if args.workload == "fullscale" else None
     roofline.update({"traffic": traffic,
+                     # one ncu --set full capture of the same kernel sources (null otherwise):
+                     # how busy the pipes that bound it were
+                     "ncu_pipes": ncu_pipes(name) if args.workload == "fullscale" else None,
                      # HBM fraction from the measured DRAM bytes of one ncu capture
                      # over the live average launch time
                      "hbm_frac_ncu_bytes": (traffic / (dom["avg_ms"] / 1000.0) / 1e9 / peak) if traffic else None,
