@@ -84,7 +84,7 @@ def test_init_by_k0_and_errors():
 # --- one Strang step on a random state (every index path) --------------------
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 16), (16, 32), (64, 16), (16, 64), (32, 32)])
+@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 16), (16, 32), (64, 16), (16, 64), (32, 32), (128, 16), (256, 16)])
 def test_one_step_random_state(prec, nx, ny):
     w = small_w(nx, ny, prec, dt=0.03)
     w["sims"][0]["qpc_h"] = 1.3
@@ -116,6 +116,47 @@ def test_three_steps_batch_of_three(prec):
         s0 = states[b].astype(np.complex64).astype(np.complex128) if prec == "c64" else states[b]
         ref = O.propagate(s0, m, 3)
         assert rel_err(pr.get_state(b), ref) <= TOL[prec] * 0.1, b
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-12), ("c64", 2e-6)])
+def test_time_reversal(prec, tol):
+    """S(-dt) S(dt) = I for the Strang product (Eq. evoloperat, symmetric
+    order): five steps forward, then five steps of a context with -dt on the
+    result, give back the starting state.  Exercises the negative-dt tables."""
+    w = small_w(64, 16, prec, dt=0.03)
+    w["sims"][0]["lam"] = 1.1
+    fwd = H().Propagator(w, init=False)
+    psi = W.random_state((64, 16, 64, 16), seed=77)
+    fwd.set_state(0, psi)
+    start = fwd.get_state(0).astype(np.complex128)
+    fwd.step(5)
+    mid = fwd.get_state(0)
+    back = H().Propagator(dict(w, dt=-w["dt"]), init=False)
+    back.set_state(0, mid)
+    back.step(5)
+    assert rel_err(back.get_state(0), start) <= tol
+    # the five steps did move the state (relative l2 change)
+    assert np.linalg.norm((mid - start).ravel()) > 0.1 * np.linalg.norm(start.ravel())
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("field", ["free", "no_field"])
+def test_degenerate_hamiltonians(prec, field):
+    """Degenerate cases of the Hamiltonian: a free particle (B = 0, no
+    confinement, no saddle, no interaction) and confinement without a
+    magnetic field (B = 0, where T_x loses its y dependence)."""
+    kw = dict(B=0.0, omega=0.0) if field == "free" else dict(B=0.0)
+    w = small_w(32, 16, prec, dt=0.03, **kw)
+    if field == "free":
+        w["sims"][0].update(qpc_h=0.0, lam=0.0)
+    pr = H().Propagator(w, init=False)
+    psi = W.random_state((32, 16, 32, 16), seed=5 if field == "free" else 6)
+    pr.set_state(0, psi)
+    pr.step(2)
+    m = A.model_for(w, w["sims"][0])
+    assert m.B == 0.0 and (m.omega == 0.0) == (field == "free")
+    s0 = psi.astype(np.complex64).astype(np.complex128) if prec == "c64" else psi
+    assert rel_err(pr.get_state(0), O.propagate(s0, m, 2)) <= TOL[prec] * 0.05
 
 
 def test_zero_steps_is_identity():
