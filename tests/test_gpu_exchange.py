@@ -223,3 +223,24 @@ def test_output_arm_entanglement(hom_runs):
     assert np.all(np.diff(anti) < -0.02)
     assert S[(1.5, 0.0, -1, 1.0)] < 0.7 * S[(1.5, 0.0, -1, 0.0)]
     assert S[(1.5, 0.0, 0, 1.0)] > 0.05
+
+
+def test_coulomb_softening_saturates():
+    """Sec. III(B), Fig. 5(b): for a product state (no exchange) the Coulomb
+    repulsion alone antibunches.  A weak interaction (large softening d of
+    Eq. coulomb) leaves P_b at the classical 1/2.  As d shrinks P_b falls,
+    but each halving of d lowers it less: in 2D the electrons find paths
+    around each other, so P_b saturates above 0 instead of vanishing."""
+    p = {}
+    for soft in (8.0, 1.0, 0.5, 0.25, 0.125):
+        w = W.sweep32(prec="c64")
+        w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=26.0, soft=soft)
+        _, obs = _run(w, [()], lambda: dict(qpc_h=1.85, qpc_w=1.5, lam=1.0, exch=0,
+                                            alpha=W.packet(-15.0, 1.5, 2.5, +1), beta=W.packet(15.0, 1.5, 2.5, -1)))
+        p[soft] = obs[0]["p_bunch"] / obs[0]["norm"]
+    print("P_b(softening):", p)
+    assert p[8.0] > 0.49
+    steps = [p[1.0] - p[0.5], p[0.5] - p[0.25], p[0.25] - p[0.125]]
+    assert p[8.0] > p[1.0] and all(d > 0 for d in steps)
+    assert steps[0] > steps[1] > steps[2]
+    assert p[0.125] > 0.3
