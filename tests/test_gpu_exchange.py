@@ -244,3 +244,30 @@ def test_coulomb_softening_saturates():
     assert p[8.0] > p[1.0] and all(d > 0 for d in steps)
     assert steps[0] > steps[1] > steps[2]
     assert p[0.125] > 0.3
+
+
+def test_bunching_dynamics():
+    """Sec. III(A): P_b(t) of the antisymmetric state is 0 while the packets
+    are apart, peaks while they meet at the saddle, then falls to a
+    stationary value that does not vanish.  The product state has no such
+    peak: it rises to its stationary 1/2, so the overshoot is an exchange
+    effect.  Sampled every 100 steps (one time unit) to t = 26."""
+    H = _binding()
+    w = W.sweep32(prec="c64")
+    w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01)
+    w["sims"] = [dict(qpc_h=1.85, qpc_w=1.5, lam=0.0, exch=e, alpha=W.packet(-15.0, 1.5, 2.5, +1),
+                      beta=W.packet(15.0, 1.5, 2.5, -1)) for e in (-1, 0)]
+    w["batch"] = 2
+    pr = H.Propagator(w)
+    pb = []
+    for _ in range(27):
+        pb.append([o["p_bunch"] / o["norm"] for o in pr.observables()])
+        pr.step(100)
+    pr.close()
+    anti, prod = np.array(pb).T
+    print("P_b(t) antisymmetric", np.round(anti, 4), "product", np.round(prod, 4))
+    assert np.all(anti[:6] < 1e-4) and np.all(prod[:6] < 1e-4)
+    assert abs(anti[-1] - anti[-3]) < 1e-4 and abs(prod[-1] - prod[-3]) < 1e-4      # stationary
+    assert anti.max() > anti[-1] + 0.03 and anti[-1] > 0.3                          # peak, no vanishing
+    assert 5 < int(np.argmax(anti)) < 20
+    assert prod.max() < prod[-1] + 1e-3                                             # no overshoot
