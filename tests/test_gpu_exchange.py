@@ -101,8 +101,9 @@ SIGMAS = (1.0, 1.5, 2.0, 2.5, 3.0)
 
 
 @pytest.fixture(scope="module")
-def hom_runs():
-    """One batch of 28 simulations, keyed (sigma, delay, exch, lam)."""
+def hom_batch():
+    """One batch of 28 simulations, keyed (sigma, delay, exch, lam): their
+    stationary P_b and the entropy of their output-arm slice."""
     w = W.sweep32(prec="c64")
     w.update(nx=256, ny=32, dx=0.5, dy=0.5, dt=0.01, t_end=26.0)
 
@@ -115,11 +116,18 @@ def hom_runs():
     keys += [(s, 0.0, 0, 0.0) for s in SIGMAS] + [(s, 0.0, -1, 0.0) for s in SIGMAS if s != 1.5]
     keys += [(1.5, d, -1, 1.0) for d in SWEEP] + [(1.5, 0.0, 0, 1.0), (1.5, 8.0, 0, 1.0)]
     _, obs = _run(w, keys, make, extra=_arm_entropy)
-    entropy.update({k: o["entropy"] for k, o in zip(keys, obs)})
-    return {k: o["p_bunch"] / o["norm"] for k, o in zip(keys, obs)}
+    return ({k: o["p_bunch"] / o["norm"] for k, o in zip(keys, obs)},
+            {k: o["entropy"] for k, o in zip(keys, obs)})
 
 
-entropy = {}   # filled by hom_runs: (sigma, delay, exch, lam) -> entropy of the output-arm slice
+@pytest.fixture(scope="module")
+def hom_runs(hom_batch):
+    return hom_batch[0]
+
+
+@pytest.fixture(scope="module")
+def arm_entropy(hom_batch):
+    return hom_batch[1]
 
 
 def test_hong_ou_mandel_dip_and_peak(hom_runs):
@@ -209,13 +217,13 @@ def test_screening_restores_exchange_driven_bunching(hom_runs):
     assert abs(screened[1.0] - free) < abs(screened[3.0] - free) < abs(full - free)
 
 
-def test_output_arm_entanglement(hom_runs):
+def test_output_arm_entanglement(arm_entropy):
     """Sec. V: the spatial entanglement between the two output arms, from the
     slice that joins them.  A product state without interaction has none;
     with exchange alone it falls as the packets get wider (it vanishes in the
     plane-wave limit); Coulomb repulsion quenches the antisymmetric state's
     entanglement, and entangles a product state on its own."""
-    S = entropy
+    S = arm_entropy
     anti = np.array([S[(s, 0.0, -1, 0.0)] for s in SIGMAS])
     print("S: antisymmetric by sigma", anti, "product", S[(1.5, 0.0, 0, 0.0)], "with Coulomb: antisymmetric",
           S[(1.5, 0.0, -1, 1.0)], "product", S[(1.5, 0.0, 0, 1.0)])
