@@ -19,12 +19,25 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hom.h"
 #include "hom_internal.h"
 
 namespace {
 
 using cd = std::complex<double>;
+
+// An NVTX range for the lifetime of the object: every entry point that
+// launches work and every kernel pass of a step is a named range, so that
+// profilers can select them (ncu --nvtx --nvtx-include).  Header-only NVTX:
+// without an attached tool a push or pop is a null-pointer check.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 6.28318530717958647692;
 constexpr size_t kAlign = 256;
@@ -640,6 +653,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     size_t ev = 0;
     hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    NvtxRange r("hom.transposing_pass");
     HOM_CUDA(c, (hom::launch_kinetic_t<T>(p.nx, p.ny, c->variant[0], a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 0)) != HOM_OK) return st;
     return HOM_OK;
@@ -659,6 +673,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     size_t ev = 0;
     hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    NvtxRange r("hom.in_place_pass");
     HOM_CUDA(c, (hom::launch_kinetic<T>(p.nx, p.ny, c->variant[1], a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 1)) != HOM_OK) return st;
     return HOM_OK;
@@ -670,6 +685,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     size_t ev = 0;
     hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    NvtxRange r("hom.transpose");
     HOM_CUDA(c, (hom::launch_transpose<T>(src, dst, p.nx * p.ny, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 2)) != HOM_OK) return st;
     return HOM_OK;
@@ -691,6 +707,7 @@ hom_status step_sequence(hom_ctx* c, char* psi, int nsteps, int sgn) {
     size_t ev = 0;
     hom_status st;
     if (c->prof && (st = prof_begin(c, &ev)) != HOM_OK) return st;
+    NvtxRange r("hom.double_pass");
     HOM_CUDA(c, (hom::launch_kinetic2<T>(p.nx, p.ny, c->variant[1], a, p.batch, c->stream)));
     if (c->prof && (st = prof_end(c, ev, 3)) != HOM_OK) return st;
     return HOM_OK;
@@ -771,6 +788,7 @@ hom_status run_steps(hom_ctx* c, char* psi, int nsteps, int sgn) {
 constexpr int kTuneMinSteps = 24;
 
 hom_status autotune(hom_ctx* c) {
+  NvtxRange range("hom_autotune");
   const bool prof_saved = c->prof;
   double ms_saved[kKinds];
   long long n_saved[kKinds];
@@ -1096,6 +1114,7 @@ hom_status hom_set_sim_params(hom_ctx* c, int32_t b, double qpc_h, double qpc_w,
 }
 
 hom_status hom_init_packets(hom_ctx* c, int32_t b, const hom_packet* alpha, const hom_packet* beta, int32_t exch) {
+  NvtxRange range("hom_init_packets");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   const hom_params& p = c->p;
@@ -1157,6 +1176,7 @@ hom_status hom_init_packets(hom_ctx* c, int32_t b, const hom_packet* alpha, cons
 }
 
 hom_status hom_step(hom_ctx* c, int32_t nsteps) {
+  NvtxRange range("hom_step");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if (nsteps < 0) return fail(c, HOM_ERR_ARG, "nsteps must be >= 0");
@@ -1181,6 +1201,7 @@ hom_status hom_step(hom_ctx* c, int32_t nsteps) {
 }
 
 hom_status hom_observables(hom_ctx* c, hom_obs* out) {
+  NvtxRange range("hom_observables");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if (!out) return fail(c, HOM_ERR_ARG, "out is NULL");
@@ -1209,6 +1230,7 @@ hom_status hom_observables(hom_ctx* c, hom_obs* out) {
 }
 
 hom_status hom_backward(hom_ctx* c, int32_t nsteps, int32_t K, double* loss, double* grad) {
+  NvtxRange range("hom_backward");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   const hom_params& p = c->p;
@@ -1316,6 +1338,7 @@ hom_status hom_copy_state(hom_ctx* c, int32_t b, void* host, size_t bytes, int32
 }
 
 hom_status hom_marginal(hom_ctx* c, double* out) {
+  NvtxRange range("hom_marginal");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   if (!out) return fail(c, HOM_ERR_ARG, "out is NULL");
@@ -1333,6 +1356,7 @@ hom_status hom_marginal(hom_ctx* c, double* out) {
 }
 
 hom_status hom_conditional(hom_ctx* c, int32_t b, int32_t ix2, int32_t iy2, double* out) {
+  NvtxRange range("hom_conditional");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   const hom_params& p = c->p;
@@ -1353,6 +1377,7 @@ hom_status hom_conditional(hom_ctx* c, int32_t b, int32_t ix2, int32_t iy2, doub
 
 hom_status hom_entanglement(hom_ctx* c, int32_t b, int32_t iy1, int32_t iy2, int32_t x1_lo, int32_t x1_hi,
                             int32_t x2_lo, int32_t x2_hi, double* entropy, double* weight) {
+  NvtxRange range("hom_entanglement");
   hom_status s = enter(c);
   if (s != HOM_OK) return s;
   const hom_params& p = c->p;
