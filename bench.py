@@ -34,6 +34,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -140,13 +141,22 @@ def fp32_peak_tflops() -> float:
 KINETIC_SOURCES = ["hom_fft.cuh", "hom_pass.cuh", "hom_kern.inc", "hom_kern_c64.cu", "hom_kern_c64_rows.cu"]
 
 
+def code_tokens(text: str) -> str:
+    """C/C++/CUDA source with its comments removed and its whitespace
+    collapsed, so that editing a comment or the layout leaves it unchanged."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash() -> str:
-    """Hash of the sources that define the kinetic passes."""
+    """Hash of the code (comments and whitespace ignored) of the sources that
+    define the kinetic passes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1903_02581_gb300", "csrc")
     for f in KINETIC_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update((f + "\n" + code_tokens(fh.read())).encode())
     return h.hexdigest()[:16]
 
 

@@ -11,13 +11,20 @@
 // K_2 acts on the (x2, y2) plane of each fixed (x1, y1): a contiguous row of
 // psi[r1][r2]; K_1 acts on the (x1, y1) planes, the rows of the transposed
 // state psi[r2][r1].  Since K_1 and K_2 commute, a step applies them in either
-// order: its first pass reads rows of whichever layout holds the state and
-// writes the transposed layout (kinetic_pass_t), its second pass works in
-// place on the rows of that layout (kinetic_pass).  The real-space phase
-// e^{-iV tau} (V1(r1) + V1(r2) + V12, symmetric in the particles) is fused
-// into the first load of a step and, for the last half step, into the last
+// order, and the host sequences the passes in one of three ways (step
+// strategies, all with the same arithmetic per element):
+//   - a transposing pass that reads rows of whichever layout holds the state
+//     and writes the other layout (kinetic_pass_t), then an in-place pass on
+//     the rows of that layout (kinetic_pass);
+//   - in-place pass, plain transpose (transpose_state), in-place pass;
+//   - a transpose and one double in-place pass per step (kinetic_pass with
+//     TWICE): the same particle's sandwich at the end of one step and at the
+//     start of the next, with the potential phase of a full step between them.
+// The real-space phase e^{-iV tau} (V1(r1) + V1(r2) + V12, symmetric in the
+// particles) is fused into the first load of a run, between the two
+// sandwiches of a double pass, and, for the last half step, into the last
 // store.  Each pass reads and writes the state once: two HBM round trips per
-// step.
+// step with the first or the third sequence.
 //
 // A CTA holds G planes of one simulation in shared memory, laid out
 // [g][x][y] with row stride RS = ny + 1 and plane stride PS (padding chosen so
