@@ -3,8 +3,10 @@
 // workspace layout, and the launch sequence of a Strang step.
 //
 // Paper: arXiv:1903.02581, Sec. II.C (Eq. evoloperat, Landau-gauge
-// Hamiltonian), Appendix A (Eq. 2PTB), Eq. coulomb, Eq. twopstate,
-// Eq. singlepwp, Eq. p_bunching.
+// Hamiltonian), Appendix A (Eq. 2PTB), Eq. coulomb, Eq. screenedCoulomb,
+// Eqs. pot_x and pot_xy (barrier blocks), Eq. H_effective (numerical edge
+// states), Eq. twopstate, Eq. singlepwp, Eq. p_bunching, and Sec. V
+// (Eq. reduced_density, the von Neumann entropy of a slice).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
