@@ -113,6 +113,32 @@ def test_strategy_two_profile_counts():
     H().hom_profile(pr.ctx, 0)
 
 
+@pytest.mark.parametrize("strategy", [0, 1, 2])
+def test_graph_replay_matches_plain_launches(strategy):
+    """hom_step captures its launches into a CUDA graph per step count and
+    replays it; with profiling on it launches the same kernels one by one
+    instead.  Both give the same state bit for bit, including the second call
+    of a step count, which replays the graph the first call captured."""
+    w = small_w(64, 32, "c64")
+    psi = W.random_state((64, 32, 64, 32), seed=31 + strategy)
+    out = []
+    for profile in (False, True):
+        pr = H().Propagator(w, init=False)
+        H().hom_autotune_set(pr.ctx, 0, 0, strategy)
+        pr.set_state(0, psi)
+        if profile:
+            H().hom_profile(pr.ctx, 1)
+        pr.step(5)
+        pr.step(5)
+        out.append(pr.get_state(0))
+        if profile:
+            assert sum(H().hom_profile_read(pr.ctx)[k] for k in ("n_transposing", "n_in_place", "n_transpose",
+                                                                "n_double")) > 0
+            H().hom_profile(pr.ctx, 0)
+        pr.close()
+    assert np.array_equal(out[0].view(np.uint8), out[1].view(np.uint8))
+
+
 def test_autotune_set_rejects_bad_choice():
     w = small_w(16, 16, "c64")
     pr = H().Propagator(w)
