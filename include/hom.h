@@ -195,7 +195,11 @@ hom_status hom_copy_state(hom_ctx* ctx, int32_t b, void* host, size_t bytes,
  * for each launch kind, the summed device milliseconds (ms[HOM_PROFILE_KINDS])
  * and launch counts (counts[HOM_PROFILE_KINDS]) since the last enable.  The
  * kinds are [0] transposing pass, [1] in-place pass, [2] transpose, [3]
- * double in-place pass.  Enabling resets the sums.  No effect on results. */
+ * double in-place pass.  Enabling resets the sums.  No effect on results.
+ * Independently of this switch, every call that launches work is an NVTX
+ * range named after the call (hom_step, hom_observables, ...), and every pass
+ * of a step a nested range: hom.transposing_pass, hom.in_place_pass,
+ * hom.transpose, hom.double_pass (for ncu --nvtx-include, for example). */
 #define HOM_PROFILE_KINDS 4
 hom_status hom_profile(hom_ctx* ctx, int32_t enable);
 hom_status hom_profile_read(hom_ctx* ctx, double* ms, int64_t* counts);
