@@ -127,7 +127,11 @@ __device__ __forceinline__ C twiddle_const(C a, int k) {
     } else {
       if (INV) { u = -a.x - a.y; w = a.x - a.y; } else { u = a.y - a.x; w = -a.x - a.y; }
     }
-    return C{fma(u, rh, u * rl), fma(w, rh, w * rl)};
+    if constexpr (sizeof(R) == 8) {
+      return C{u * rh, w * rh};           // FP64: no low part (a product by 0 would still be issued)
+    } else {
+      return C{fma(u, rh, u * rl), fma(w, rh, w * rl)};
+    }
   }
   const int j = k * (16 / N);
   const C hi{hi_part<R>(cos16(j)), hi_part<R>(-sin16(j))};
