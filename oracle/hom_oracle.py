@@ -94,7 +94,11 @@ phases, cyclotron motion, Strang/Lie convergence orders, time reversal,
 energy conservation, Coulomb expectation by quadrature, packet energy,
 adjoint dot-product test and finite differences, marginals and conditional
 slices of product and Slater states in closed form, entropies of states with
-known Schmidt coefficients).
+known Schmidt coefficients, the saddle of R3 by its height, its value one
+width away, its moments on a fine grid and its expectation in Gaussian
+packets, dV/dtheta against differences of the potential, and the factor order
+of the Strang and printed first-order steps against dense matrix
+exponentials built from numpy's FFT).
 """
 
 from __future__ import annotations
@@ -255,21 +259,30 @@ def ty_total(m: Model) -> np.ndarray:
 # Time step (Eq. evoloperat, Appendix A; R2)
 # ----------------------------------------------------------------------------
 
-def strang_step(psi: np.ndarray, m: Model, dt: float | None = None,
-                vtot: np.ndarray | None = None) -> np.ndarray:
-    """One symmetric split step, factor by factor, right to left."""
+def strang_phases(m: Model, dt: float | None = None,
+                  vtot: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """The three diagonal factors of one Strang step as arrays:
+    e^{-i V dt/2} (real space), e^{-i T_x dt/2} (k_x, y) and e^{-i T_y dt} (k_y).
+    They are the same every step, so a long run may compute them once."""
     dt = m.dt if dt is None else dt
     V = v_total(m) if vtot is None else vtot
+    return (np.exp(-0.5j * dt * V), np.exp(-0.5j * dt * tx_total(m)), np.exp(-1j * dt * ty_total(m)))
+
+
+def strang_step(psi: np.ndarray, m: Model, dt: float | None = None,
+                vtot: np.ndarray | None = None, phases=None) -> np.ndarray:
+    """One symmetric split step, factor by factor, right to left."""
+    pv, ptx, pty = strang_phases(m, dt, vtot) if phases is None else phases
     X, Y = (AXIS_X1, AXIS_X2), (AXIS_Y1, AXIS_Y2)
-    psi = np.exp(-0.5j * dt * V) * psi                  # e^{-i V dt/2}      (real space)
+    psi = pv * psi                                      # e^{-i V dt/2}      (real space)
     psi = dft_pair(psi, X)                              # F_{x1,x2}: -> (k_x, y)
-    psi = np.exp(-0.5j * dt * tx_total(m)) * psi        # e^{-i T_x dt/2}
+    psi = ptx * psi                                     # e^{-i T_x dt/2}
     psi = dft_pair(psi, Y)                              # F_{y1,y2}: -> (k_x, k_y)
-    psi = np.exp(-1j * dt * ty_total(m)) * psi          # e^{-i T_y dt}
+    psi = pty * psi                                     # e^{-i T_y dt}
     psi = dft_pair(psi, Y, inverse=True)                # F^-1_{y1,y2}
-    psi = np.exp(-0.5j * dt * tx_total(m)) * psi        # e^{-i T_x dt/2}
+    psi = ptx * psi                                     # e^{-i T_x dt/2}
     psi = dft_pair(psi, X, inverse=True)                # F^-1_{x1,x2}: -> real space
-    psi = np.exp(-0.5j * dt * V) * psi                  # e^{-i V dt/2}
+    psi = pv * psi                                      # e^{-i V dt/2}
     return psi
 
 
@@ -292,9 +305,13 @@ def lie_step(psi: np.ndarray, m: Model, dt: float | None = None,
 def propagate(psi: np.ndarray, m: Model, nsteps: int, order: str = "strang",
               dt: float | None = None) -> np.ndarray:
     V = v_total(m)
-    step = strang_step if order == "strang" else lie_step
+    if order == "strang":
+        ph = strang_phases(m, dt, V)
+        for _ in range(nsteps):
+            psi = strang_step(psi, m, dt, phases=ph)
+        return psi
     for _ in range(nsteps):
-        psi = step(psi, m, dt, vtot=V)
+        psi = lie_step(psi, m, dt, vtot=V)
     return psi
 
 

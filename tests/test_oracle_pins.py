@@ -518,3 +518,130 @@ def test_numerical_packet_without_wall_is_the_closed_form_packet():
     a = O.edge_packet(m, -2.0, 1.3, 1.1)
     b = O.edge_packet_numeric(m, -2.0, 1.3, 1.1)
     assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(a))
+
+
+# --- R3: the Gaussian saddle standing in for the QPC, by value and moments ---
+
+def test_qpc_saddle_height_and_width_by_value():
+    # cell-centred grid x_j = (j - 7.5) * 0.5: x0 = 0.25 is x_8, and x0 -+ w with
+    # w = 1 are x_6 and x_10.  With omega = 0 the potential is the saddle alone.
+    h, w, x0 = 1.3, 1.0, 0.25
+    m = O.Model(nx=16, ny=16, dx=0.5, dy=0.5, omega=0.0, lam=0.0, qpc_h=h, qpc_w=w, qpc_x0=x0)
+    x = O.coords(m.nx, m.dx)
+    assert x[8] == x0 and x[6] == x0 - w and x[10] == x0 + w
+    v = O.v1(m)
+    assert np.max(np.abs(v - v[:, :1])) == 0.0                # no y dependence without confinement
+    assert abs(v[8, 0] - h) <= 1e-15                           # the height at the centre
+    # w is the standard deviation: one width away the saddle is down by e^{-1/2}
+    for j in (6, 10):
+        assert abs(v[j, 0] - h * math.exp(-0.5)) <= 1e-15
+    assert abs(v[0, 0] - h * math.exp(-0.5 * ((x[0] - x0) / w) ** 2)) <= 1e-15 * h
+    assert v[0, 0] < 1e-3 * h                                   # far away: nothing left
+
+
+def test_qpc_saddle_moments_on_a_fine_grid():
+    # integral h w sqrt(2 pi), mean x0 and variance w^2 of the saddle profile:
+    # the moments that make w a standard deviation and h a height
+    h, w, x0 = 0.8, 0.9, 0.37
+    m = O.Model(nx=1024, ny=16, dx=0.02, dy=0.5, omega=0.0, lam=0.0, qpc_h=h, qpc_w=w, qpc_x0=x0)
+    x = O.coords(m.nx, m.dx)
+    v = O.v1(m)[:, 0]
+    area = np.sum(v) * m.dx
+    mean = np.sum(x * v) * m.dx / area
+    var = np.sum((x - mean) ** 2 * v) * m.dx / area
+    assert abs(area - h * w * math.sqrt(2 * math.pi)) <= 1e-12
+    assert abs(mean - x0) <= 1e-12
+    assert abs(var - w * w) <= 1e-12
+
+
+def test_qpc_saddle_expectation_of_gaussian_packets():
+    # <V1(r1) + V1(r2)> of a product of two normalised Gaussians with x
+    # densities N(mu_i, s_i^2): the Gaussian convolution
+    #   E[h exp(-(X - x0)^2 / 2w^2)] = h w / sqrt(w^2 + s^2) exp(-(mu - x0)^2 / 2(w^2 + s^2)),
+    # checked against scipy quad of the same expectation first
+    h, w, x0 = 1.7, 0.8, 0.3
+    m = O.Model(nx=128, ny=16, dx=0.125, dy=0.5, omega=0.0, lam=0.0, qpc_h=h, qpc_w=w, qpc_x0=x0)
+    x = O.coords(m.nx, m.dx)
+    y = O.coords(m.ny, m.dy)
+    parts = [(-0.9, 0.45), (1.2, 0.6)]
+
+    def packet(mu, s):
+        phi = np.exp(-((x[:, None] - mu) ** 2) / (4 * s * s) - y[None, :] ** 2 / 2.0).astype(np.complex128)
+        return phi / math.sqrt(np.sum(np.abs(phi) ** 2) * m.dx * m.dy)
+
+    psi = np.einsum("ab,cd->abcd", packet(*parts[0]), packet(*parts[1]))
+    got = O.observables(psi, m)["e_pot"]
+    closed = sum(h * w / math.sqrt(w * w + s * s) * math.exp(-((mu - x0) ** 2) / (2 * (w * w + s * s)))
+                 for mu, s in parts)
+    for mu, s in parts:
+        q, _ = integrate.quad(lambda t: math.exp(-((t - mu) ** 2) / (2 * s * s)) / math.sqrt(2 * math.pi * s * s)
+                              * h * math.exp(-((t - x0) ** 2) / (2 * w * w)), -np.inf, np.inf,
+                              epsabs=1e-14, epsrel=1e-13)
+        one = h * w / math.sqrt(w * w + s * s) * math.exp(-((mu - x0) ** 2) / (2 * (w * w + s * s)))
+        assert abs(q - one) <= 1e-12
+    assert abs(got - closed) <= 1e-12
+
+
+def test_dv_dtheta_is_the_derivative_of_the_potential():
+    m = O.Model(nx=32, ny=16, dx=0.5, dy=0.5, qpc_h=1.2, qpc_w=1.4, qpc_x0=0.3)
+    eps = 1e-5
+
+    def four_d(a):
+        return a[:, :, None, None] + a[None, None, :, :]
+
+    fd = {"h": four_d(O.v1(m, h=m.qpc_h + eps) - O.v1(m, h=m.qpc_h - eps)) / (2 * eps),
+          "w": four_d(O.v1(m, w=m.qpc_w + eps) - O.v1(m, w=m.qpc_w - eps)) / (2 * eps)}
+    for k, ref in fd.items():
+        got = O.dv_dtheta(m, k)
+        assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref)), k
+
+
+# --- R2 and the printed product: factor order against dense exponentials ----
+
+def _dense_factors(m):
+    """T_x, T_y (sums over both particles) and V as dense Hermitian matrices on
+    the 4D index (x1, y1, x2, y2), built from numpy's FFT of the identity and
+    numpy's fftfreq, so that their exponentials (scipy.linalg.expm) give the
+    factors of a split step with no code of the oracle but v_total."""
+    nx, ny = m.nx, m.ny
+    n = nx * ny
+    y = (np.arange(ny) - (ny - 1) / 2.0) * m.dy
+    kx = 2 * np.pi * np.fft.fftfreq(nx, d=m.dx)
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d=m.dy)
+    Fx, Fy = np.fft.fft(np.eye(nx), axis=0), np.fft.fft(np.eye(ny), axis=0)
+    t1x = np.zeros((n, n), dtype=np.complex128)
+    t1y = np.zeros((n, n), dtype=np.complex128)
+    for j in range(ny):
+        blk = np.linalg.inv(Fx) @ np.diag(0.5 * (kx - m.B * y[j]) ** 2) @ Fx
+        t1x[j::ny, j::ny] = blk
+    tyb = np.linalg.inv(Fy) @ np.diag(0.5 * ky ** 2) @ Fy
+    for i in range(nx):
+        t1y[i * ny:(i + 1) * ny, i * ny:(i + 1) * ny] = tyb
+    eye = np.eye(n)
+    Tx = np.kron(t1x, eye) + np.kron(eye, t1x)
+    Ty = np.kron(t1y, eye) + np.kron(eye, t1y)
+    V = np.diag(O.v_total(m).reshape(-1)).astype(np.complex128)
+    return Tx, Ty, V
+
+
+def test_step_factor_orders_against_dense_exponentials():
+    from scipy.linalg import expm
+    m = O.Model(nx=8, ny=4, dx=0.6, dy=0.7, B=1.3, omega=0.9, dt=0.3, qpc_h=1.1, qpc_w=1.2,
+                qpc_x0=0.2, lam=0.8, soft=0.5)
+    Tx, Ty, V = _dense_factors(m)
+    dt = m.dt
+    E = lambda A, s: expm(-1j * s * A)
+    psi = W.random_state((m.nx, m.ny, m.nx, m.ny), seed=21)
+    v = psi.reshape(-1)
+    strang = E(V, dt / 2) @ E(Tx, dt / 2) @ E(Ty, dt) @ E(Tx, dt / 2) @ E(V, dt / 2) @ v
+    lie = E(V, dt) @ E(Ty, dt) @ E(Tx, dt) @ v             # Eq. evoloperat: T_x first, then T_y, then V
+    got_s = O.strang_step(psi, m).reshape(-1)
+    got_l = O.lie_step(psi, m).reshape(-1)
+    scale = np.max(np.abs(v))
+    assert np.max(np.abs(got_s - strang)) <= 1e-12 * scale
+    assert np.max(np.abs(got_l - lie)) <= 1e-12 * scale
+    # the orders are distinguishable at this dt: every other order of the
+    # printed product misses by far more than the tolerance
+    for other in (E(V, dt) @ E(Tx, dt) @ E(Ty, dt), E(Ty, dt) @ E(Tx, dt) @ E(V, dt),
+                  E(Tx, dt) @ E(V, dt) @ E(Ty, dt)):
+        assert np.max(np.abs(got_l - other @ v)) > 1e-3 * scale
