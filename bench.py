@@ -13,14 +13,16 @@ of the observables (norm, energy terms, bunching probability).
            time), inputs resident in HBM, max time over ranks;
   e2e    = the same metric through the C ABI with the state copied from
            pinned host memory every step and the observables read back;
-  roofline = the dominant kernel's algorithmic work over its average
-           CUDA-event duration: bytes (16 B per point per pass in complex64:
-           one read, one write) against the measured HBM copy bandwidth, and
-           FP32 flops against the FP32 peak of the SM count and clock; the
-           line reports whichever fraction is higher as the bound; its
-           traffic (DRAM bytes) and ncu_pipes (FMA pipe, issue, L1 data
-           pipe and DRAM utilisation) come from the committed ncu summary of
-           the same kernel sources, and are null for any other sources;
+  roofline = the dominant kernel's algorithmic bytes (16 B per point per
+           launch in complex64: one read, one write) over its average
+           CUDA-event duration, against the measured HBM copy bandwidth; beside
+           it (roofline.alu) its FP32 flops against this GPU's FMA rate
+           measured by the library's own throughput kernel.  The per-launch
+           durations come from a profiled run of the same bench steps after
+           the timed region (the timed region replays CUDA graphs).  traffic
+           (DRAM bytes) and ncu_pipes (FMA pipe, issue, L1 data pipe and DRAM
+           utilisation) come from the committed ncu summary of the same kernel
+           sources, and are null for any other sources;
   cpu_baseline = the FP64 oracle on the host cores on a bounded sample.
 
 Multi-GPU: one process per GPU (torchrun); each rank propagates its own
@@ -33,6 +35,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -124,18 +127,6 @@ def sandwich_flops(nx: int, ny: int, fp64: bool = False) -> float:
 
 
 VPHASE_FLOPS = 22.0   # three deltas combined (two complex products, four adds) and applied
-
-
-def fp32_peak_tflops() -> float:
-    """Nominal FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
-    at the maximum SM clock of the GB300s."""
-    mhz = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", mhz))
-    except Exception:
-        pass
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
 KINETIC_SOURCES = ["hom_fft.cuh", "hom_pass.cuh", "hom_kern.inc", "hom_kern_c64.cu", "hom_kern_c64_rows.cu"]
@@ -286,14 +277,42 @@ def oracle_sample_rate(steps: int = 1, workload: str = "fullscale"):
     return pts * steps / sec, sec, desc
 
 
-def precision_study(device: str):
-    """FP32 vs FP64 on the sweep32 workload (6 simulations, 32x32 per electron,
-    1000 steps): time to solution and error of P_b, norm and energy against
-    the FP64 oracle's stored observables (tests/golden/sweep32_oracle.json,
-    written by tests/golden/make_golden.py from the oracle only)."""
+def _timed_run(w: dict, device: str, nsteps: int):
+    """Observables after nsteps of workload w and the seconds the steps and the
+    observables took (graph replay; module load and capture in a warm-up run)."""
     import torch
 
     from paper_1903_02581_gb300 import binding as H
+
+    pr = H.Propagator(w, device=device)
+    pr.step(nsteps)
+    pr.observables()
+    pr.close()
+    pr = H.Propagator(w, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pr.step(nsteps)
+    obs = pr.observables()
+    sec = time.perf_counter() - t0
+    pr.close()
+    return obs, sec
+
+
+def precision_study(device: str):
+    """FP32 against FP64 at equal bunching-probability accuracy on the sweep32
+    workload (6 simulations, 32x32 per electron, t = 5), plus both precisions
+    at an HBM-resident size.
+
+    Accuracy of a run = |P_b - P_b(dt -> 0)| with P_b(dt -> 0) the Richardson
+    extrapolation (4 P(dt/2) - P(dt)) / 3 of complex128 runs at dt = 0.005 and
+    0.0025 (the Strang product is second order).  complex64 runs at the
+    workload's dt = 0.005; complex128 at dt = 0.02, 0.01, 0.005 and 0.0025.
+    The FP64 run matched to FP32 is the largest dt whose worst error over the
+    6 simulations is no larger than complex64's; time to solution is the
+    device time of all steps plus the observables.  Errors against the FP64
+    oracle's stored observables at dt = 0.005 (tests/golden/sweep32_oracle.json,
+    written by tests/golden/make_golden.py from the oracle only) are reported
+    beside them."""
     from paper_1903_02581_gb300 import workloads as W
 
     path = os.path.join(ROOT, "tests", "golden", "sweep32_oracle.json")
@@ -301,41 +320,48 @@ def precision_study(device: str):
         return None
     with open(path) as f:
         gold = json.load(f)
-    out = {"workload": "sweep32: 6 simulations x 32x32 per electron (1,048,576 points each), 1000 steps",
-           "reference": "FP64 oracle (numpy) observables after 1000 steps"}
-    for prec in ("c64", "c128"):
+    T = 5.0
+    out = {"workload": "sweep32: 6 simulations x 32x32 per electron (1,048,576 points each), t = 5",
+           "reference": "FP64 oracle (numpy) observables at dt = 0.005 after 1000 steps",
+           "accuracy": "|P_b - P_b(dt->0)|, P_b(dt->0) Richardson-extrapolated from complex128 at dt 0.005/0.0025"}
+    runs = {}
+    for prec, dt in (("c64", 0.005), ("c128", 0.02), ("c128", 0.01), ("c128", 0.005), ("c128", 0.0025)):
         w = W.sweep32(prec=prec)
-        pr = H.Propagator(w, device=device)
-        o0 = pr.observables()
-        pr.step(1)                       # warm-up (graph capture, module load)
-        pr.close()
-        pr = H.Propagator(w, device=device)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pr.step(w["nsteps"])
-        obs = pr.observables()
-        sec = time.perf_counter() - t0
-        pts = (w["nx"] * w["ny"]) ** 2 * len(w["sims"])
-        errs = [abs(o["p_bunch"] - g["obs"]["1000"]["p_bunch"]) for o, g in zip(obs, gold["sims"])]
-        errs_n = [abs(o["p_bunch"] / o["norm"] - g["obs"]["1000"]["p_bunch"] / g["obs"]["1000"]["norm"])
-                  for o, g in zip(obs, gold["sims"])]
-        nd = [abs(o["norm"] - 1.0) for o in obs]
-        ed = [abs(o["energy"] - a["energy"]) / abs(a["energy"]) for o, a in zip(obs, o0)]
-        eo = [abs(o["energy"] - g["obs"]["1000"]["energy"]) / abs(g["obs"]["1000"]["energy"])
-              for o, g in zip(obs, gold["sims"])]
-        out[prec] = {"seconds": sec, "updates_per_s": pts * w["nsteps"] / sec,
-                     "max_abs_p_bunch_err_vs_oracle": max(errs),
-                     "max_abs_normalised_p_bunch_err_vs_oracle": max(errs_n), "max_norm_drift": max(nd),
-                     "max_rel_energy_drift": max(ed), "max_rel_energy_err_vs_oracle": max(eo)}
-        pr.close()
-    out["fp32_speedup"] = out["c64"]["updates_per_s"] / out["c128"]["updates_per_s"]
-    # complex128 is bound by the FP64 pipe: algorithmic FP64 flops per point
-    # per step (two sandwiches and the potential) against the nominal 1.25 TF/s
-    w = W.sweep32(prec="c128")
-    f64 = 2 * sandwich_flops(w["nx"], w["ny"], fp64=True) + VPHASE_FLOPS
-    out["c128"]["fp64_flops_per_point_step"] = f64
-    out["c128"]["fp64_tflops"] = out["c128"]["updates_per_s"] * f64 / 1e12
-    out["c128"]["fp64_frac_of_nominal_1.25_tflops"] = out["c128"]["fp64_tflops"] / 1.25
+        w["dt"] = dt
+        n = int(round(T / dt))
+        obs, sec = _timed_run(w, device, n)
+        runs[(prec, dt)] = (obs, sec, n)
+    pts = (32 * 32) ** 2 * 6
+    limit = [(4 * b["p_bunch"] - a["p_bunch"]) / 3.0
+             for a, b in zip(runs[("c128", 0.005)][0], runs[("c128", 0.0025)][0])]
+    table = []
+    for (prec, dt), (obs, sec, n) in runs.items():
+        g = [s_["obs"]["1000"] for s_ in gold["sims"]]
+        table.append({"prec": prec, "dt": dt, "steps": n, "seconds": sec, "updates_per_s": pts * n / sec,
+                      "max_abs_p_bunch_err": max(abs(o["p_bunch"] - l) for o, l in zip(obs, limit)),
+                      "max_abs_p_bunch_err_vs_oracle_dt0.005": max(abs(o["p_bunch"] - a["p_bunch"])
+                                                                   for o, a in zip(obs, g)),
+                      "max_norm_drift": max(abs(o["norm"] - 1.0) for o in obs)})
+    out["runs"] = table
+    f32 = next(r for r in table if r["prec"] == "c64")
+    ok = [r for r in table if r["prec"] == "c128" and r["max_abs_p_bunch_err"] <= f32["max_abs_p_bunch_err"]]
+    if ok:
+        m64 = max(ok, key=lambda r: r["dt"])
+        out["equal_accuracy"] = {"c64_dt": f32["dt"], "c64_err": f32["max_abs_p_bunch_err"],
+                                 "c64_seconds": f32["seconds"], "c128_dt": m64["dt"],
+                                 "c128_err": m64["max_abs_p_bunch_err"], "c128_seconds": m64["seconds"],
+                                 "fp32_speedup_at_equal_accuracy": m64["seconds"] / f32["seconds"]}
+    # both precisions on one HBM-resident grid: the full-scale workload at
+    # 128x64 per electron (complex128: 1 GiB, the largest plane it supports)
+    hbm = {}
+    for prec in ("c64", "c128"):
+        w = W.shrink(W.fullscale(), nx=128)
+        w["prec"] = prec
+        obs, sec = _timed_run(w, device, 24)
+        hbm[prec] = {"seconds_24_steps": sec, "updates_per_s": (128 * 64) ** 2 * 24 / sec,
+                     "state_gib": (128 * 64) ** 2 * (8 if prec == "c64" else 16) / 2 ** 30}
+    hbm["fp32_speedup"] = hbm["c64"]["updates_per_s"] / hbm["c128"]["updates_per_s"]
+    out["hbm_resident_128x64"] = hbm
     return out
 
 
@@ -413,15 +439,20 @@ def gb300_arm(args):
         pr.step(args.inner)
         return pr.observables()
 
+    # measured arithmetic peaks of this GPU (the kinetic passes' ALU roofline)
+    sink = torch.zeros(4, dtype=torch.float64, device=f"cuda:{local}")
+    fp32_peak = H.hom_alu_peak(0, sink.data_ptr(), stream.cuda_stream) / 1e12
+    fp64_peak = H.hom_alu_peak(1, sink.data_ptr(), stream.cuda_stream) / 1e12
+
     for _ in range(args.warmup):
         bench_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # timed region: the production path (each hom_step replays its CUDA graph)
     sampler = ClockSampler(local)
     sampler.start()
-    H.hom_profile(pr.ctx, True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -433,56 +464,79 @@ def gb300_arm(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    prof = H.hom_profile_read(pr.ctx)
-    tuning = H.hom_autotune_info(pr.ctx)
-    H.hom_profile(pr.ctx, False)
     clocks = sampler.stop()
     ms_max = RP.slowest(ev0.elapsed_time(ev1), device=f"cuda:{local}")
     value = RP.job_rate(world, batch, pts, args.inner * args.steps, ms_max / 1000.0)
 
+    # per-kernel split: the same bench steps again, launched pass by pass with
+    # a CUDA-event pair around every kernel on the context's stream (hom_profile)
+    H.hom_profile(pr.ctx, True)
+    evp0 = torch.cuda.Event(enable_timing=True)
+    evp1 = torch.cuda.Event(enable_timing=True)
+    evp0.record(stream)
+    for _ in range(args.steps):
+        bench_step()
+    evp1.record(stream)
+    torch.cuda.synchronize()
+    prof = H.hom_profile_read(pr.ctx)
+    tuning = H.hom_autotune_info(pr.ctx)
+    H.hom_profile(pr.ctx, False)
+    ms_profiled = evp0.elapsed_time(evp1)
+
     # dominant kernel and its roofline.  Algorithmic bytes: one read and one
-    # write of the state per launch.  Algorithmic FP32 flops: one kinetic
-    # sandwich per point (two plus the potential phase in the double pass).
+    # write of the state per launch (16 B per point in complex64).  Algorithmic
+    # FP32 flops per point: the survey's count for one Strang step,
+    # 10 log2(points) + 50 (5 N log2 N per FFT, ~50 for the phases), which is
+    # what the double pass computes (two sandwiches of one particle and the
+    # potential); and the kernels' own count of their FP32 operations.
     algo_bytes = batch * pts * 8 * 2
     sw = sandwich_flops(w["nx"], w["ny"])
-    kinds = [("kinetic_pass_t", prof["ms_transposing"], prof["n_transposing"], sw),
-             ("kinetic_pass", prof["ms_in_place"], prof["n_in_place"], sw),
-             ("transpose_state", prof["ms_transpose"], prof["n_transpose"], 0.0),
-             ("kinetic_pass_double", prof["ms_double"], prof["n_double"], 2 * sw + VPHASE_FLOPS)]
+    survey_step = 10.0 * math.log2(pts) + 50.0
+    kinds = [("kinetic_pass_t", prof["ms_transposing"], prof["n_transposing"], sw, survey_step / 2),
+             ("kinetic_pass", prof["ms_in_place"], prof["n_in_place"], sw, survey_step / 2),
+             ("transpose_state", prof["ms_transpose"], prof["n_transpose"], 0.0, 0.0),
+             ("kinetic_pass_double", prof["ms_double"], prof["n_double"], 2 * sw + VPHASE_FLOPS, survey_step)]
     peak, peak_kind = load_peaks()
-    fpeak = fp32_peak_tflops()
     per_kernel = {}
-    for k, t, c_, fl in kinds:
+    for k, t, c_, fl, fs in kinds:
         if not c_:
             continue
         avg = t / c_ / 1000.0
-        per_kernel[k] = {"launches": c_, "avg_ms": avg * 1000.0,
+        per_kernel[k] = {"launches": c_, "avg_ms": avg * 1000.0, "share": t / max(sum(q[1] for q in kinds), 1e-12),
                          "hbm_gbs": algo_bytes / avg / 1e9, "hbm_frac": algo_bytes / avg / 1e9 / peak,
-                         "fp32_tflops": fl * batch * pts / avg / 1e12,
-                         "fp32_frac": fl * batch * pts / avg / 1e12 / fpeak,
-                         "flops_per_point": fl}
-    name, tot_ms, cnt, _ = max(kinds, key=lambda k: k[1])
+                         "fp32_tflops_kernel_count": fl * batch * pts / avg / 1e12,
+                         "fp32_frac_kernel_count": fl * batch * pts / avg / 1e12 / fp32_peak,
+                         "fp32_tflops_survey_count": fs * batch * pts / avg / 1e12,
+                         "fp32_frac_survey_count": fs * batch * pts / avg / 1e12 / fp32_peak,
+                         "flops_per_point_kernel_count": fl, "flops_per_point_survey_count": fs}
+    name, tot_ms, cnt, _, _ = max(kinds, key=lambda k: k[1])
     dom = per_kernel[name]
-    if dom["fp32_frac"] > dom["hbm_frac"]:
-        roofline = {"bound": "alu", "achieved": dom["fp32_tflops"], "peak": fpeak, "unit": "TFLOP/s",
-                    "frac": dom["fp32_frac"], "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
-    else:
-        roofline = {"bound": "hbm", "achieved": dom["hbm_gbs"], "peak": peak, "unit": "GB/s",
-                    "frac": dom["hbm_frac"], "peak_source": peak_kind}
-    step_ms = sum(k[1] for k in kinds) / max(args.steps * args.inner, 1)
     traffic = ncu_traffic(name) if args.workload == "fullscale" else None
-    roofline.update({"traffic": traffic,
-                     # one ncu --set full capture of the same kernel sources (null otherwise):
-                     # how busy the pipes that bound it were
-                     "ncu_pipes": ncu_pipes(name) if args.workload == "fullscale" else None,
-                     # HBM fraction from the measured DRAM bytes of one ncu capture
-                     # over the live average launch time
-                     "hbm_frac_ncu_bytes": (traffic / (dom["avg_ms"] / 1000.0) / 1e9 / peak) if traffic else None,
-                     "kernel": name, "kernels": per_kernel,
-                     "hbm_peak_gbs": peak,
-                     # the two-round-trip floor: 32 B per point per step (complex64)
-                     "step_algorithmic_hbm_frac": 2 * algo_bytes / (step_ms / 1000.0) / 1e9 / peak,
-                     "step_ms": step_ms, "autotune": tuning})
+    roofline = {"bound": "hbm", "achieved": dom["hbm_gbs"], "peak": peak, "unit": "GB/s", "frac": dom["hbm_frac"],
+                "traffic": traffic, "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy)",
+                # what actually limits the kinetic passes: FP32 arithmetic and
+                # instruction issue, against this GPU's measured FMA rate
+                "alu": {"achieved_tflops_survey_count": dom["fp32_tflops_survey_count"],
+                        "achieved_tflops_kernel_count": dom["fp32_tflops_kernel_count"],
+                        "peak_tflops": fp32_peak, "frac_survey_count": dom["fp32_frac_survey_count"],
+                        "frac_kernel_count": dom["fp32_frac_kernel_count"],
+                        "peak_source": "measured: hom_alu_peak FP32 FMA throughput kernel, best of 3"},
+                "fp64_peak_tflops_measured": fp64_peak,
+                "sms": torch.cuda.get_device_properties(local).multi_processor_count}
+    step_ms = sum(k[1] for k in kinds) / max(args.steps * args.inner, 1)
+    roofline.update({
+        # one ncu --set full capture of the same kernel sources (null otherwise):
+        # how busy the pipes that bound it were
+        "ncu_pipes": ncu_pipes(name) if args.workload == "fullscale" else None,
+        "hbm_frac_ncu_bytes": (traffic / (dom["avg_ms"] / 1000.0) / 1e9 / peak) if traffic else None,
+        "kernel": name, "kernels": per_kernel, "hbm_peak_gbs": peak,
+        # the two-round-trip floor: 32 B per point per Strang step (complex64),
+        # over the step time of the graph-replayed timed region
+        "step_algorithmic_hbm_frac": 2 * algo_bytes / (ms_max / 1000.0 / (args.steps * args.inner)) / 1e9 / peak,
+        "step_ms_graph": ms_max / (args.steps * args.inner),
+        "step_ms_profiled_kernels": step_ms,
+        "ms_per_bench_step_profiled": ms_profiled / args.steps,
+        "autotune": tuning})
 
     # end to end through the C ABI: host state in pinned memory copied in every step
     e2e = None

@@ -276,9 +276,14 @@ hom_status hom_vn_entropy(const double* phi, int32_t m1, int32_t m2, double* ent
  *   1 <= batch <= 64 (HOM_ERR_ARG otherwise, nothing launched).
  * Its partial sums live in one fixed 256 KiB array in the library's device
  * memory (every GPU that loads the library holds it until the process exits);
- * nothing is allocated, by the library or by the caller.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current: make that first call before any stream capture.  Every
+ * nothing is allocated, by the library or by the caller.  The first call in a
+ * CUDA context (normally the device's primary context) looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current and keeps it
+ * for that context: make that first call before any stream capture.  The kept
+ * address assumes the context stays alive: after cudaDeviceReset, or anything
+ * else that destroys the device's primary context, do not call this entry
+ * point again in the same process (the new context may reuse the handle, and
+ * the kept address would then be stale).  Every
  * call writes every partial it later reads, so no clearing is needed, but all
  * calls share the array: calls whose kernels overlap on the GPU (different
  * streams, or several host threads) race and must be serialised by the
@@ -286,6 +291,20 @@ hom_status hom_vn_entropy(const double* phi, int32_t m1, int32_t m2, double* ent
  * default stream).  HOM_ERR_CUDA if a launch or the address lookup fails. */
 hom_status hom_bunching_static(const void* d_state, int32_t prec, int32_t nx, int32_t ny, int32_t batch,
                                double dx, double dy, double* d_out, void* cuda_stream);
+
+/* Measured arithmetic peak of the current device, for the roofline of the
+ * kinetic passes (which are bound by FP32 arithmetic, not by HBM).  A
+ * measurement utility, not a step of the paper's method.
+ *   kind 0: FP32 fused multiply-adds, kind 1: FP64; *flops_per_s receives the
+ *   best of three timed launches (after one warm-up) of a kernel in which
+ *   every thread of 8 CTAs per SM runs 8 independent FMA chains (2 flops per
+ *   FMA), each launch about 10 ms at the nominal rates;
+ *   d_sink: device, >= 16 bytes, caller-owned; written only on a value the
+ *   chains never reach, so in practice never;
+ *   synchronous: waits for its launches on cuda_stream (NULL = legacy default).
+ * HOM_ERR_ARG for a bad kind or NULL pointer, HOM_ERR_CUDA if a launch or an
+ * event call fails.  Allocates no device memory. */
+hom_status hom_alu_peak(int32_t kind, void* d_sink, void* cuda_stream, double* flops_per_s);
 
 /* Message of the last failure on ctx (or of the last failed hom_create when
  * ctx is NULL); never NULL. */

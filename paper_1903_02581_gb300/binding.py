@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
     L.hom_vn_entropy.argtypes = [P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double),
                                  P(ctypes.c_double)]
     L.hom_vn_entropy.restype = ctypes.c_int
+    L.hom_alu_peak.argtypes = [ctypes.c_int32, vp, vp, P(ctypes.c_double)]
+    L.hom_alu_peak.restype = ctypes.c_int
     L.hom_last_error.argtypes = [vp]
     L.hom_last_error.restype = ctypes.c_char_p
     L.hom_destroy.argtypes = [vp]
@@ -237,6 +239,16 @@ def hom_autotune_info(ctx) -> dict:
 def hom_autotune_set(ctx, variant_transposing: int, variant_in_place: int, strategy: int) -> None:
     ch = (ctypes.c_int32 * 3)(variant_transposing, variant_in_place, strategy)
     _check(lib().hom_autotune_set(ctx, ch), ctx)
+
+
+def hom_alu_peak(kind: int, d_sink: int, stream: int = 0) -> float:
+    """Measured FMA rate of the current GPU in flops/s: kind 0 FP32, 1 FP64.
+    d_sink: a device buffer of at least 16 bytes (never written in practice)."""
+    out = ctypes.c_double(0.0)
+    st = lib().hom_alu_peak(kind, d_sink, stream or None, ctypes.byref(out))
+    if st != HOM_OK:
+        raise HomError(st, "hom_alu_peak failed")
+    return out.value
 
 
 def hom_last_error(ctx) -> str:

@@ -780,7 +780,7 @@ struct AccHook {
   bool by_first;                  // x hook: w[pos * NY + y]; y hook: w[y position]
   __device__ __forceinline__ C operator()(int p, int q, C v) {
     const double wt = by_first ? w[p * NY + q] : w[q];
-    acc += wt * (double)cnorm2(v);
+    acc += wt * cnorm2_d(v);
     return v;
   }
 };
@@ -829,7 +829,7 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
     const C v = base[off];
     if constexpr (!COL) {
       const int r1 = t0 + g, r2 = r;
-      const double rho = (double)cnorm2(v);
+      const double rho = cnorm2_d(v);
       const int x1 = r1 / NY, y1 = r1 % NY, x2 = r2 / NY, y2 = r2 % NY;
       s_norm += rho;
       s_pot += rho * (v1[r1] + v1[r2]);

@@ -13,8 +13,11 @@
 // The scratch array is a file-scope __device__ array: every GPU that loads the
 // library holds it (kStaticMaxBatch * kStaticBlocks * 2 doubles = 256 KiB)
 // until the process exits.  In host code its name is only a stand-in, not a
-// device address, so the address is fetched with cudaGetSymbolAddress once
-// per device, with that device current, on the first call made on it.
+// device address, so the address is fetched with cudaGetSymbolAddress with the
+// device current, on the first call made in a CUDA context, and kept per
+// context: each context that loads the library has its own copy of the array
+// at its own address.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -26,12 +29,32 @@ namespace {
 constexpr int kStaticMaxBatch = 64;   // simulations per call
 constexpr int kStaticBlocks = 256;    // partial sums per simulation
 constexpr int kStaticThreads = 256;
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 static __device__ __align__(256) double g_static_scratch[kStaticMaxBatch * kStaticBlocks * 2];
 
-double* g_scratch_addr[kMaxDevices] = {};
+// Set-up results: the array's address in each CUDA context seen so far.
+struct ScratchSlot {
+  CUcontext ctx;
+  double* addr;
+};
+ScratchSlot g_slots[kMaxContexts] = {};
+int g_nslots = 0;
 std::mutex g_scratch_mutex;
+
+// cuCtxGetCurrent, looked up once through the runtime (no link to the driver library).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(f);
+  }
+  return fn;
+}
 
 __device__ __forceinline__ double block_total(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -86,17 +109,29 @@ __global__ void static_finish(const double* __restrict__ scratch, double dV, dou
 
 bool pow2_between(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array in the current context: looked up with
+// cudaGetSymbolAddress on the first call in a context (the set-up), then taken
+// from the table.  A context the table has no room for is looked up on every call.
 hom_status scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HOM_ERR_CUDA;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return HOM_ERR_CUDA;
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return HOM_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return HOM_ERR_CUDA;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+  if (ctx) {
+    for (int i = 0; i < g_nslots; ++i)
+      if (g_slots[i].ctx == ctx) {
+        *out = g_slots[i].addr;
+        return HOM_OK;
+      }
   }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return HOM_ERR_CUDA;
+  // with no context current before, the runtime has just made the device's
+  // primary context current
+  if (!ctx && get(&ctx) != CUDA_SUCCESS) return HOM_ERR_CUDA;
+  if (ctx && g_nslots < kMaxContexts) g_slots[g_nslots++] = ScratchSlot{ctx, static_cast<double*>(p)};
+  *out = static_cast<double*>(p);
   return HOM_OK;
 }
 

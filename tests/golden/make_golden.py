@@ -1,13 +1,25 @@
-"""Write the golden observables used by the precision study and GPU tests.
+"""Write the golden observables and sampled states used by the precision
+study and the GPU tests.
 
 Calls only the FP64 oracle (oracle/); every stored value is the oracle's.
-Usage: python tests/golden/make_golden.py sweep32   (writes sweep32_oracle.json)
+Usage:
+  python tests/golden/make_golden.py sweep32     -> sweep32_oracle.json
+  python tests/golden/make_golden.py fullscale2  -> fullscale2_oracle.json + .npz
+      the full-scale workload (256x64 per electron, Coulomb strength 1,
+      softening 0.25, packets of width 2) after 2 Strang steps: observables
+      and 12 sampled rows psi[r1, :] (r1 = x1*ny + y1 fixed, all r2)
+  python tests/golden/make_golden.py batched     -> batched_oracle.json + .npz
+      simulations 0 and 31 of the batched sweep (128x32 per electron) over
+      all 1500 steps: observables every few hundred steps and 8 sampled rows
+      of each final state
 """
 
 import json
 import os
 import sys
 import time
+
+import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
@@ -40,8 +52,77 @@ def sweep32():
     return out
 
 
+def sampled_rows(psi, nrand, seed, extra=()):
+    """Row indices r1 of psi[r1, r2] to store: the rows of largest norm (where
+    the state is), nrand seeded random rows and any extra ones, sorted."""
+    n = psi.shape[0] * psi.shape[1]
+    flat = psi.reshape(n, n)
+    norms = np.sum(np.abs(flat) ** 2, axis=1)
+    top = list(np.argsort(norms)[::-1][:8])
+    rng = np.random.default_rng(seed)
+    rows = set(int(r) for r in top) | set(int(r) for r in rng.choice(n, size=nrand, replace=False)) | set(extra)
+    rows = sorted(rows)
+    return rows, flat[rows]
+
+
+def fullscale2():
+    """Two Strang steps of the full-scale workload from the oracle's own
+    initial state (the state the library builds from the same packets)."""
+    w = W.fullscale(sigma=2.0)
+    sim = w["sims"][0]
+    m = A.model_for(w, sim)
+    t0 = time.time()
+    psi = A.initial_state(w, sim)
+    obs = {"0": O.observables(psi, m)}
+    print(f"initial state and observables: {time.time() - t0:.0f}s", flush=True)
+    ph = O.strang_phases(m)
+    for i in range(2):
+        psi = O.strang_step(psi, m, phases=ph)
+        print(f"step {i + 1}: {time.time() - t0:.0f}s", flush=True)
+    del ph
+    obs["2"] = O.observables(psi, m)
+    ny = w["ny"]
+    # the periodic x edge (x1 = 0 and nx - 1) and the saddle (x1 = nx/2) at the
+    # packets' edge row y1 = 37 besides the largest and random rows
+    rows, vals = sampled_rows(psi, 4, 3, extra=(0 * ny + 37, (w["nx"] - 1) * ny + 37, (w["nx"] // 2) * ny + 37))
+    print(f"done: {time.time() - t0:.0f}s, P_b = {obs['2']['p_bunch']:.15f}", flush=True)
+    np.savez(os.path.join(HERE, "fullscale2_oracle.npz"), rows=np.array(rows), psi_rows=vals)
+    return {"workload": "fullscale", "sigma": 2.0, "nx": w["nx"], "ny": w["ny"], "dt": w["dt"], "nsteps": 2,
+            "rows": rows, "obs": obs}
+
+
+def batched():
+    """Simulations 0 (Coulomb off) and 31 (Coulomb on) of the batched sweep."""
+    w = W.batched()
+    out = {"workload": "batched", "nx": w["nx"], "ny": w["ny"], "dt": w["dt"], "nsteps": w["nsteps"],
+           "checkpoints": [0, 100, 500, 1000, 1500], "sims": {}}
+    arrays = {}
+    for b in (0, 31):
+        sim = w["sims"][b]
+        m = A.model_for(w, sim)
+        t0 = time.time()
+        psi = A.initial_state(w, sim)
+        ph = O.strang_phases(m)
+        rec = {"lam": sim["lam"], "sigma": sim["alpha"]["sigma"], "beta_x0": sim["beta"]["x0"], "obs": {}}
+        done = 0
+        for c in out["checkpoints"]:
+            for _ in range(c - done):
+                psi = O.strang_step(psi, m, phases=ph)
+            done = c
+            rec["obs"][str(c)] = O.observables(psi, m)
+            print(f"sim {b} step {c}: {time.time() - t0:.0f}s P_b = {rec['obs'][str(c)]['p_bunch']:.15f}",
+                  flush=True)
+        rows, vals = sampled_rows(psi, 0, 7 + b)
+        rec["rows"] = rows
+        arrays[f"rows_{b}"] = np.array(rows)
+        arrays[f"psi_rows_{b}"] = vals
+        out["sims"][str(b)] = rec
+    np.savez(os.path.join(HERE, "batched_oracle.npz"), **arrays)
+    return out
+
+
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "sweep32"
-    res = {"sweep32": sweep32}[which]()
+    res = {"sweep32": sweep32, "fullscale2": fullscale2, "batched": batched}[which]()
     with open(os.path.join(HERE, f"{which}_oracle.json"), "w") as f:
         json.dump(res, f, indent=1)
