@@ -65,10 +65,24 @@ __device__ __forceinline__ constexpr double sin16(int j) { return cos16(j + 12);
 // v * (1 + d): a unit-modulus phase stored as its deviation d = w - 1 from 1.
 // For the small phase angles of a split step, d carries the phase with full
 // relative precision, so the rounded table has |1 + d| = 1 to far better than
-// the precision of w itself; the product costs the same four FMAs.
+// the precision of w itself.
 template <typename C>
 __device__ __forceinline__ C apply_delta(C v, C d) {
   return C{fma(v.x, d.x, fma(-v.y, d.y, v.x)), fma(v.x, d.y, fma(v.y, d.x, v.y))};
+}
+// In FP32 the correction t = v * d is formed first, at its own (small) scale,
+// and added to v in one rounding.  The FMA chain above instead adds the
+// second-order term v * d.x (|d.x| = 2 sin^2(theta/2)) to an already rounded
+// value in a rounding of its own; where |v * d.x| is within a few ulps of v,
+// as for the most occupied low-k modes at the time steps used, that rounding
+// is biased with a sign set by the phase angle, the same every step, and the
+// norm drifts by ~1e-8 per step.  With t added once, the rounding error is
+// that of v + t, whose low bits vary over many ulps: no measurable drift.
+template <>
+__device__ __forceinline__ float2 apply_delta<float2>(float2 v, float2 d) {
+  const float tr = fmaf(v.x, d.x, -(v.y * d.y));
+  const float ti = fmaf(v.y, d.x, v.x * d.y);
+  return __fadd2_rn(v, make_float2(tr, ti));
 }
 
 // v * (hi + lo) (or v * conj(hi + lo)): a twiddle carried as an unevaluated

@@ -3,11 +3,12 @@ complex128 and complex64 against the FP64 oracle's stored observables
 (tests/golden/sweep32_oracle.json, written by make_golden.py from the oracle
 only).
 
-complex128: every observable to 1e-10.  complex64: the bunching probability of
-the state the run holds, P_b / norm, to 1e-6; the norm itself to 2e-5.  In
-FP32 the norm of the state drifts by about 1e-8 per step (rounding of the
-transform arithmetic, correlated from step to step); the unnormalised sum P_b
-carries that drift, which is why the comparison divides it out."""
+complex128: every observable to 1e-10.  complex64: the bunching probability
+P_b (the raw sum of Eq. p_bunching, not divided by the norm) to 1e-6 at every
+checkpoint, the norm to 2e-6 and the energy to 1e-5 relative.  The FP32 phase
+products form their small correction first and add it in one rounding (see
+apply_delta in hom_fft.cuh); with the earlier FMA chain the norm drifted by
+~1e-8 per step and P_b missed 1e-6 after 1000 steps."""
 
 import json
 import os
@@ -52,6 +53,6 @@ def test_sweep32_matches_oracle_observables(gold, prec):
                 for k in ("norm", "energy", "e_kin", "e_pot", "e_coul", "p_bunch"):
                     assert abs(o[k] - ref[k]) <= 1e-10 * max(1.0, abs(ref[k])), (c, k, o[k], ref[k])
             else:
-                pb = o["p_bunch"] / o["norm"]
-                assert abs(pb - ref["p_bunch"] / ref["norm"]) <= 1e-6, (c, pb, ref["p_bunch"])
-                assert abs(o["norm"] - ref["norm"]) <= 2e-5, (c, o["norm"])
+                assert abs(o["p_bunch"] - ref["p_bunch"]) <= 1e-6, (c, o["p_bunch"], ref["p_bunch"])
+                assert abs(o["norm"] - ref["norm"]) <= 2e-6, (c, o["norm"])
+                assert abs(o["energy"] - ref["energy"]) <= 1e-5 * abs(ref["energy"]), (c, o["energy"])
