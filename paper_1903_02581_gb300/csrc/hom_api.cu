@@ -323,7 +323,9 @@ hom_status build_shared_tables(hom_ctx* c) {
         const bool lie = p.split == HOM_LIE;
         const cd q = phase_delta((lie ? 1.0 : 0.5) * dt * t);
         put(qa, dbl, (size_t)px * ny + j, q);
-        put(qt, dbl, (size_t)j * nx + px, lie ? cd(0.0, 0.0) : q);
+        // after the y sandwich, with the 1/(nx ny) of both inverse transforms
+        // folded in (a power of two: the scaled delta is exact)
+        put(qt, dbl, (size_t)j * nx + px, lie ? cd(0.0, 0.0) : q / ((double)nx * ny));
         if (sgn == 0) tx[(size_t)px * ny + j] = t;
       }
     }

@@ -85,6 +85,21 @@ __device__ __forceinline__ float2 apply_delta<float2>(float2 v, float2 d) {
   return __fadd2_rn(v, make_float2(tr, ti));
 }
 
+// s v (1 + d) from a table holding ds = s d, with s a power of two (the
+// 1/(nx ny) of both inverse transforms).  Scaling by a power of two commutes
+// with rounding, so this gives the bits of apply_delta(s v, d) with one
+// product fewer per component.
+template <typename C>
+__device__ __forceinline__ C apply_delta_scaled(C v, typename Re<C>::type s, C ds) {
+  return C{fma(v.x, ds.x, fma(-v.y, ds.y, v.x * s)), fma(v.x, ds.y, fma(v.y, ds.x, v.y * s))};
+}
+template <>
+__device__ __forceinline__ float2 apply_delta_scaled<float2>(float2 v, float s, float2 ds) {
+  const float tr = fmaf(v.x, ds.x, -(v.y * ds.y));
+  const float ti = fmaf(v.y, ds.x, v.x * ds.y);
+  return __ffma2_rn(v, make_float2(s, s), make_float2(tr, ti));
+}
+
 // v * (hi + lo) (or v * conj(hi + lo)): a twiddle carried as an unevaluated
 // sum of two values, so that its modulus is 1 to twice the working precision.
 // Rounding a unit twiddle to one FP32 value leaves |w| != 1 by up to 6e-8,

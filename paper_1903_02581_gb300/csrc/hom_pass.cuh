@@ -44,7 +44,7 @@ template <typename C> struct PassArgs {
   C* psi;              // state [batch][n][n]
   // Unit-modulus phase tables are stored as deltas d = w - 1 (see apply_delta).
   const C* qa;         // e^{-i dt/4 (k_x - B y)^2} - 1        [x position][y]
-  const C* qt;         // the same table transposed            [y][x position]
+  const C* qt;         // the same deltas times 1/(nx ny), transposed [y][x position]
   const C* gy;         // e^{-i dt/2 k_y^2} - 1                [y position]
   const C* twx;        // e^{-2 pi i j / nx}, j < nx: interleaved (hi, lo) pairs
   const C* twy;        // e^{-2 pi i j / ny}, j < ny: interleaved (hi, lo) pairs
@@ -192,9 +192,10 @@ __device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
 }
 
 // The y part of the kinetic sandwich on every y-line: F_y, G, F_y^-1 (no
-// 1/ny), then the second T_x/2 phase qb (a [y][x position] table, so that
-// lanes running over x positions read consecutive entries) and the 1/(nx ny)
-// of both inverse transforms (a power of two: exact).
+// 1/ny), then the second T_x/2 phase and the 1/(nx ny) of both inverse
+// transforms (a power of two: exact) from qb, a [y][x position] table of the
+// scaled deltas (so that lanes running over x positions read consecutive
+// entries; see apply_delta_scaled).
 template <typename C, int NX, int NY, int G, int NT, int RS, int PS>
 __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restrict__ gy,
                                            const C* __restrict__ qb) {
@@ -215,7 +216,7 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
       for (int k = 0; k < NY; ++k) v[k] = apply_delta(v[k], ldg(gy + k));
       dft_reg<NY, true>(v);
 #pragma unroll
-      for (int y = 0; y < NY; ++y) row[y] = apply_delta(C{v[y].x * scale, v[y].y * scale}, ldg(qb + y * NX + px));
+      for (int y = 0; y < NY; ++y) row[y] = apply_delta_scaled(v[y], scale, ldg(qb + y * NX + px));
     }
     __syncthreads();
   } else {
@@ -256,7 +257,7 @@ __device__ __forceinline__ void y_sandwich(C* sm, const C* tw, const C* __restri
 #pragma unroll
       for (int m2 = 0; m2 < N1; ++m2) {
         const int y = m1 + N2 * m2;
-        row[y] = apply_delta(C{v[m2].x * scale, v[m2].y * scale}, ldg(qb + y * NX + px));
+        row[y] = apply_delta_scaled(v[m2], scale, ldg(qb + y * NX + px));
       }
     };
     // Each warp owns LW whole lines when that keeps every half-warp on 16
