@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-tc-trial", action="store_true")
     ap.add_argument("--workload", default="fullscale", choices=["fullscale", "batched"],
                     help="fullscale: one 256x64 simulation (the headline); batched: 32 simulations of 128x32")
     ap.add_argument("--pin", default=None,
@@ -365,6 +366,40 @@ def precision_study(device: str):
     return out
 
 
+def tc_trial(device: str, sm_mhz: float, sms: int):
+    """The tensor-core y sandwich (hom_ysandwich_tc, a design trial) on the
+    full-scale plane count's worth of 64-point lines: device time per launch,
+    cycles per 256-line plane (the unit the FFT form's 12.3 k cycles per plane
+    were measured in), and on the first 8192 lines its error and mean norm
+    change per line against numpy's FFT in FP64."""
+    import numpy as np
+    import torch
+
+    from paper_1903_02581_gb300 import binding as H
+
+    nplanes, dt, dy = 4096, 0.002, 0.25
+    nlines = nplanes * 256
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal((nlines, 64)) + 1j * rng.standard_normal((nlines, 64))).astype(np.complex64)
+    d_in = torch.from_numpy(x).to(device)
+    d_out = torch.empty_like(d_in)
+    wb = H.lib().hom_ysandwich_tc_work_bytes()
+    work = torch.empty(wb, dtype=torch.uint8, device=device)
+    ms = H.hom_ysandwich_tc(d_in.data_ptr(), d_out.data_ptr(), nlines, dt, dy, work.data_ptr(), wb, 5)
+    k = 2 * np.pi * np.fft.fftfreq(64, d=dy)
+    x64 = x[:8192].astype(np.complex128)
+    ref = np.fft.ifft(np.exp(-0.5j * dt * k * k)[None, :] * np.fft.fft(x64, axis=1), axis=1)
+    got = d_out[:8192].cpu().numpy().astype(np.complex128)
+    n0 = np.sum(np.abs(x64) ** 2, axis=1)
+    ch = (np.sum(np.abs(got) ** 2, axis=1) - n0) / n0
+    return {"lines": nlines, "ms_per_launch": ms,
+            "cycles_per_256_line_plane": ms * 1e-3 * sm_mhz * 1e6 * sms / nplanes,
+            "fft_form_cycles_per_plane": 12.3e3,
+            "tensor_tflops_bf16": 6 * 2 * 128 * 128 * nlines / (ms * 1e-3) / 1e12,
+            "max_err_rel": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "mean_norm_change_per_line": float(np.mean(ch)), "rms_norm_change_per_line": float(np.sqrt(np.mean(ch ** 2)))}
+
+
 def run_config(w: dict, wname: str, inner: int, world: int) -> dict:
     """The ``config`` object of the JSON line, shared by both arms."""
     pts = (w["nx"] * w["ny"]) ** 2
@@ -575,6 +610,10 @@ def gb300_arm(args):
     if rank == 0 and world == 1 and not args.no_precision:
         precision = precision_study(f"cuda:{local}")
 
+    trial = None
+    if rank == 0 and world == 1 and not args.no_tc_trial:
+        trial = tc_trial(f"cuda:{local}", (clocks or {}).get("sm_mhz", 2070.0), roofline["sms"])
+
     launches = args.steps * 4 + sum(k[2] for k in kinds)
     if rank == 0:
         line = {
@@ -584,7 +623,7 @@ def gb300_arm(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": run_config(w, wname, args.inner, world),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "precision": precision, "p_bunch_last": obs[0]["p_bunch"] if obs else None,
+            "clocks": clocks, "precision": precision, "tc_trial": trial, "p_bunch_last": obs[0]["p_bunch"] if obs else None,
             "norm_last": obs[0]["norm"] if obs else None,
         }
         print(json.dumps(line), flush=True)

@@ -306,6 +306,26 @@ hom_status hom_bunching_static(const void* d_state, int32_t prec, int32_t nx, in
  * event call fails.  Allocates no device memory. */
 hom_status hom_alu_peak(int32_t kind, void* d_sink, void* cuda_stream, double* flops_per_s);
 
+/* Tensor-core form of the y part of the kinetic sandwich (F_y^-1 e^{-i dt T_y}
+ * F_y with the 1/64 of the inverse transform, Eq. evoloperat) for ny = 64: a
+ * design trial that measures whether the short-axis DFT as a dense product
+ * on the tensor cores (tcgen05.mma, bf16 operands split three ways, FP32
+ * accumulation) beats the FFT form; hom_step does not use it.
+ *   d_in, d_out: device, nlines lines of 64 complex64 values (interleaved,
+ *                16-byte aligned), d_out = each line times the circulant;
+ *   nlines: a positive multiple of 128;
+ *   dt, dy: the time step and the y spacing of the T_y phase;
+ *   d_work: device, >= hom_ysandwich_tc_work_bytes() bytes, 16-byte aligned,
+ *           caller-owned (the split operator and an error flag);
+ *   nrep: timed launches after one warm-up; *ms (may be NULL) receives
+ *         their average device time (CUDA events on cuda_stream).
+ * Synchronous.  HOM_ERR_ARG for bad sizes or pointers, HOM_ERR_CUDA for a
+ * failed launch, HOM_ERR_TIMEOUT if a CTA's bounded wait for its products
+ * gave up (it frees its tensor memory and returns). */
+size_t hom_ysandwich_tc_work_bytes(void);
+hom_status hom_ysandwich_tc(const float* d_in, float* d_out, int32_t nlines, double dt, double dy, void* d_work,
+                            size_t work_bytes, int32_t nrep, float* ms, void* cuda_stream);
+
 /* Message of the last failure on ctx (or of the last failed hom_create when
  * ctx is NULL); never NULL. */
 const char* hom_last_error(const hom_ctx* ctx);

@@ -115,6 +115,11 @@ def lib() -> ctypes.CDLL:
     L.hom_vn_entropy.restype = ctypes.c_int
     L.hom_alu_peak.argtypes = [ctypes.c_int32, vp, vp, P(ctypes.c_double)]
     L.hom_alu_peak.restype = ctypes.c_int
+    L.hom_ysandwich_tc_work_bytes.argtypes = []
+    L.hom_ysandwich_tc_work_bytes.restype = ctypes.c_size_t
+    L.hom_ysandwich_tc.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, vp, ctypes.c_size_t,
+                                   ctypes.c_int32, P(ctypes.c_float), vp]
+    L.hom_ysandwich_tc.restype = ctypes.c_int
     L.hom_last_error.argtypes = [vp]
     L.hom_last_error.restype = ctypes.c_char_p
     L.hom_destroy.argtypes = [vp]
@@ -249,6 +254,18 @@ def hom_alu_peak(kind: int, d_sink: int, stream: int = 0) -> float:
     if st != HOM_OK:
         raise HomError(st, "hom_alu_peak failed")
     return out.value
+
+
+def hom_ysandwich_tc(d_in: int, d_out: int, nlines: int, dt: float, dy: float, d_work: int, work_bytes: int,
+                     nrep: int = 1, stream: int = 0) -> float:
+    """Tensor-core y sandwich of nlines 64-point lines (design trial); returns
+    the average device ms of nrep launches."""
+    ms = ctypes.c_float(0.0)
+    st = lib().hom_ysandwich_tc(d_in, d_out, nlines, dt, dy, d_work, work_bytes, nrep, ctypes.byref(ms),
+                                stream or None)
+    if st != HOM_OK:
+        raise HomError(st, "hom_ysandwich_tc failed")
+    return ms.value
 
 
 def hom_last_error(ctx) -> str:

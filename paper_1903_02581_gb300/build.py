@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 UNITS = ["hom_api.cu", "hom_kern_c64.cu", "hom_kern_c64_rows.cu", "hom_kern_c128.cu", "hom_kern_c128_rows.cu",
          "hom_observe.cu",
-         "hom_static.cu", "hom_peak.cu"]
+         "hom_static.cu", "hom_peak.cu", "hom_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

@@ -24,8 +24,11 @@ template <> struct Re<double2> { using type = double; };
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
 // FP32 complex add/subtract as one packed two-lane instruction (sm_100 family);
-// each lane rounds to nearest exactly as the scalar add does.
-template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// each lane rounds to nearest exactly as the scalar add does (a + 1 * b is
+// the exact sum before its one rounding).
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(1.0f, 1.0f), a);
+}
 template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
