@@ -3,12 +3,15 @@ trial of the short-axis DFT as a dense product on tcgen05 with bf16 operands
 split three ways): each 64-point line times F_y^-1 e^{-i dt T_y} F_y, against
 the oracle's DFT and kinetic phase in FP64 on seeded random lines.
 
-Tolerance: 1e-6 of the largest output value.  The split keeps the products
-down to 2^-16 of the leading one, so the dropped terms are ~2^-24 relative
-(2.6e-8 measured on the CPU with exact accumulation), and the output is
-rounded to FP32 once; 1e-6 leaves room for the accumulation order.  The mean
-change of a line's norm (the operator is unitary) is reported, because a bias
-there, the same every step, is what would decide the trial for the propagator.
+Tolerance: 48 x 2^-23 = 5.7e-6 of the largest output value.  The split keeps
+the products down to 2^-16 of the leading one, so the dropped terms are
+~2^-24 relative (2.6e-8 on the CPU with exact accumulation); what remains is
+the tensor core's FP32 accumulation, at most one accumulator ulp (2^-23) per
+accumulation step of the 6 x 8 = 48 steps.  The mean change of a line's norm
+(the operator is unitary) is reported and bounded by twice that: a bias
+there, the same every step, is what decides the trial for the propagator
+(on a GB300 it is -1.6e-6 per application, against +1e-10 for the same split
+with exact accumulation, so the FFT form stays in the kinetic passes).
 """
 
 import numpy as np
@@ -44,8 +47,8 @@ def test_tensor_core_y_sandwich_matches_oracle_operator():
     n0 = np.sum(np.abs(x64) ** 2, axis=1)
     bias = float(np.mean((np.sum(np.abs(got) ** 2, axis=1) - n0) / n0))
     print(f"tensor-core y sandwich: max error {err:.3e} of max|y|, mean norm change per line {bias:+.3e}")
-    assert err <= 1e-6, err
-    assert abs(bias) <= 1e-6, bias
+    assert err <= 48 * 2.0 ** -23, err
+    assert abs(bias) <= 2 * 48 * 2.0 ** -23, bias
 
 
 def test_tensor_core_y_sandwich_rejects_bad_sizes():
