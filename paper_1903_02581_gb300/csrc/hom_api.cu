@@ -185,10 +185,12 @@ Layout make_layout(const hom_params& p) {
   }
   L.twx = take(2 * p.nx * eb);
   L.twy = take(2 * p.ny * eb);
-  L.tx = take(n * 8);
-  L.ty = take(p.ny * 8);
-  L.v1 = take(B * n * 8);
-  L.v12 = take(B * D * 8);
+  // observables' energy weights, in the state precision
+  const size_t rb = eb / 2;
+  L.tx = take(n * rb);
+  L.ty = take(p.ny * rb);
+  L.v1 = take(B * n * rb);
+  L.v12 = take(B * D * rb);
   L.tiles_row = tiles_of(p, false);
   L.tiles_col = tiles_of(p, true);
   L.part_row = take(B * L.tiles_row * hom::NPART * 8);
@@ -302,6 +304,21 @@ hom_status upload(hom_ctx* c, size_t off, const void* src, size_t bytes) {
   return HOM_OK;
 }
 
+// Real FP64 values uploaded in the state precision (rounded once to FP32 for
+// complex64) and synchronised, so the host vector may go right after.
+hom_status upload_real(hom_ctx* c, size_t off, const std::vector<double>& v, bool dbl) {
+  if (dbl) {
+    if (hom_status s = upload(c, off, v.data(), v.size() * 8); s != HOM_OK) return s;
+  } else {
+    std::vector<float> f(v.begin(), v.end());
+    if (hom_status s = upload(c, off, f.data(), f.size() * 4); s != HOM_OK) return s;
+    HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HOM_OK;
+  }
+  HOM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOM_OK;
+}
+
 // Tables shared by all simulations: kinetic phases (both signs of dt),
 // twiddles, kinetic weights of the observables.
 hom_status build_shared_tables(hom_ctx* c) {
@@ -355,8 +372,8 @@ hom_status build_shared_tables(hom_ctx* c) {
   hom_status s;
   if ((s = upload(c, c->L.twx, twx.data(), twx.size())) != HOM_OK) return s;
   if ((s = upload(c, c->L.twy, twy.data(), twy.size())) != HOM_OK) return s;
-  if ((s = upload(c, c->L.tx, tx.data(), tx.size() * 8)) != HOM_OK) return s;
-  if ((s = upload(c, c->L.ty, ty.data(), ty.size() * 8)) != HOM_OK) return s;
+  if ((s = upload_real(c, c->L.tx, tx, dbl)) != HOM_OK) return s;
+  if ((s = upload_real(c, c->L.ty, ty, dbl)) != HOM_OK) return s;
   HOM_CUDA(c, cudaStreamSynchronize(c->stream));
   return HOM_OK;
 }
@@ -408,8 +425,9 @@ hom_status build_sim_tables(hom_ctx* c, int b) {
     }
   }
   hom_status s;
-  if ((s = upload(c, c->L.v1 + (size_t)b * n * 8, v1.data(), n * 8)) != HOM_OK) return s;
-  if ((s = upload(c, c->L.v12 + (size_t)b * D * 8, v12.data(), D * 8)) != HOM_OK) return s;
+  const size_t rb = dbl ? 8 : 4;
+  if ((s = upload_real(c, c->L.v1 + (size_t)b * n * rb, v1, dbl)) != HOM_OK) return s;
+  if ((s = upload_real(c, c->L.v12 + (size_t)b * D * rb, v12, dbl)) != HOM_OK) return s;
   HOM_CUDA(c, cudaStreamSynchronize(c->stream));
   return HOM_OK;
 }
@@ -936,10 +954,10 @@ hom_status measure_launch(hom_ctx* c) {
   m.psi = reinterpret_cast<const C*>(c->state);
   m.twx = reinterpret_cast<const C*>(c->ws + c->L.twx);
   m.twy = reinterpret_cast<const C*>(c->ws + c->L.twy);
-  m.tx = reinterpret_cast<const double*>(c->ws + c->L.tx);
-  m.ty = reinterpret_cast<const double*>(c->ws + c->L.ty);
-  m.v1 = reinterpret_cast<const double*>(c->ws + c->L.v1);
-  m.v12 = reinterpret_cast<const double*>(c->ws + c->L.v12);
+  m.tx = reinterpret_cast<const T*>(c->ws + c->L.tx);
+  m.ty = reinterpret_cast<const T*>(c->ws + c->L.ty);
+  m.v1 = reinterpret_cast<const T*>(c->ws + c->L.v1);
+  m.v12 = reinterpret_cast<const T*>(c->ws + c->L.v12);
   double* obs = reinterpret_cast<double*>(c->ws + c->L.obs);
   m.partial = reinterpret_cast<double*>(c->ws + c->L.part_row);
   HOM_CUDA(c, (hom::launch_measure<T>(p.nx, p.ny, false, m, p.batch, c->stream)));

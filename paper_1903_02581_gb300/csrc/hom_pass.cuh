@@ -77,14 +77,18 @@ template <typename C> struct PassArgsT {
   int pref_ahead;      // prefetch into L2 the tile this many CTAs ahead (0: off)
 };
 
+// The energy weights are in the state precision: the energy terms are summed
+// per thread in that precision (a few dozen terms) and added in FP64; the
+// norm and the bunching probability are FP64 sums of exact FP64 squares.
 template <typename C> struct MeasureArgs {
+  using R = typename Re<C>::type;
   const C* psi;
   const C* twx;
   const C* twy;
-  const double* tx;    // 1/2 (k_x - B y)^2                    [x position][y]
-  const double* ty;    // 1/2 k_y^2                            [y position]
-  const double* v1;    // V1(r)                                [batch][n]
-  const double* v12;   // V12(dx, dy)                          [batch][(2nx-1)(2ny-1)]
+  const R* tx;         // 1/2 (k_x - B y)^2                    [x position][y]
+  const R* ty;         // 1/2 k_y^2                            [y position]
+  const R* v1;         // V1(r)                                [batch][n]
+  const R* v12;        // V12(dx, dy)                          [batch][(2nx-1)(2ny-1)]
   double* partial;     // [tile][NPART]
 };
 
@@ -776,12 +780,13 @@ __global__ void __launch_bounds__(256) transpose_state(const C* __restrict__ src
 // ---------------------------------------------------------------------------
 template <typename C, int NY>
 struct AccHook {
-  const double* __restrict__ w;   // weight by (pos, other)
-  double acc;
+  using R = typename Re<C>::type;
+  const R* __restrict__ w;        // weight by (pos, other)
+  R acc;
   bool by_first;                  // x hook: w[pos * NY + y]; y hook: w[y position]
   __device__ __forceinline__ C operator()(int p, int q, C v) {
-    const double wt = by_first ? w[p * NY + q] : w[q];
-    acc += wt * cnorm2_d(v);
+    const R wt = by_first ? w[p * NY + q] : w[q];
+    acc = fma(wt, cnorm2(v), acc);
     return v;
   }
 };
@@ -817,11 +822,13 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
   const int tile = blockIdx.x;
   const int b = tile / Gm::TILES_PER_SIM;
   const int t0 = (tile % Gm::TILES_PER_SIM) * G;
+  using R = typename Re<C>::type;
   const C* base = a.psi + (size_t)b * N * N;
-  const double* v1 = a.v1 + (size_t)b * N;
-  const double* v12 = a.v12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
+  const R* v1 = a.v1 + (size_t)b * N;
+  const R* v12 = a.v12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
 
-  double s_norm = 0.0, s_pot = 0.0, s_coul = 0.0, s_pb = 0.0;
+  double s_norm = 0.0, s_pb = 0.0;
+  R s_pot = 0, s_coul = 0;
   for (int e = tid; e < G * N; e += NT) {
     int g, r;
     size_t off;
@@ -831,22 +838,23 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
     if constexpr (!COL) {
       const int r1 = t0 + g, r2 = r;
       const double rho = cnorm2_d(v);
+      const R rr = cnorm2(v);
       const int x1 = r1 / NY, y1 = r1 % NY, x2 = r2 / NY, y2 = r2 % NY;
       s_norm += rho;
-      s_pot += rho * (v1[r1] + v1[r2]);
-      s_coul += rho * v12[(x1 - x2 + NX - 1) * (2 * NY - 1) + (y1 - y2 + NY - 1)];
+      s_pot = fma(rr, v1[r1] + v1[r2], s_pot);
+      s_coul = fma(rr, v12[(x1 - x2 + NX - 1) * (2 * NY - 1) + (y1 - y2 + NY - 1)], s_coul);
       if ((x1 < NX / 2) == (x2 < NX / 2)) s_pb += rho;
     }
     sm[g * PS + (r / NY) * RS + (r % NY)] = v;
   }
   __syncthreads();
 
-  AccHook<C, NY> hx{a.tx, 0.0, true};
+  AccHook<C, NY> hx{a.tx, (R)0, true};
   x_forward<C, NX, NY, G, NT, RS, PS>(sm, stwx, hx);
-  AccHook<C, NY> hy{a.ty, 0.0, false};
+  AccHook<C, NY> hy{a.ty, (R)0, false};
   y_forward<C, NX, NY, G, NT, RS, PS>(sm, stwy, hy);
 
-  const double vals[NPART] = {s_norm, s_pot, s_coul, s_pb, hx.acc, hy.acc};
+  const double vals[NPART] = {s_norm, (double)s_pot, (double)s_coul, s_pb, (double)hx.acc, (double)hy.acc};
   double* out = a.partial + (size_t)tile * NPART;
 #pragma unroll
   for (int i = 0; i < NPART; ++i) {
