@@ -520,17 +520,17 @@ def gb300_arm(args):
 
     # dominant kernel and its roofline.  Algorithmic bytes: one read and one
     # write of the state per launch (16 B per point in complex64).  Algorithmic
-    # FP32 flops per point: the survey's count for one Strang step,
-    # 10 log2(points) + 50 (5 N log2 N per FFT, ~50 for the phases), which is
-    # what the double pass computes (two sandwiches of one particle and the
-    # potential); and the kernels' own count of their FP32 operations.
+    # FP32 flops per point: the textbook count for one Strang step,
+    # 10 log2(points) + 50 (5 N log2 N per complex FFT, ~50 for the phases),
+    # which is what the double pass computes (two sandwiches of one particle
+    # and the potential); and the kernels' own count of their FP32 operations.
     algo_bytes = batch * pts * 8 * 2
     sw = sandwich_flops(w["nx"], w["ny"])
-    survey_step = 10.0 * math.log2(pts) + 50.0
-    kinds = [("kinetic_pass_t", prof["ms_transposing"], prof["n_transposing"], sw, survey_step / 2),
-             ("kinetic_pass", prof["ms_in_place"], prof["n_in_place"], sw, survey_step / 2),
+    nlogn_step = 10.0 * math.log2(pts) + 50.0
+    kinds = [("kinetic_pass_t", prof["ms_transposing"], prof["n_transposing"], sw, nlogn_step / 2),
+             ("kinetic_pass", prof["ms_in_place"], prof["n_in_place"], sw, nlogn_step / 2),
              ("transpose_state", prof["ms_transpose"], prof["n_transpose"], 0.0, 0.0),
-             ("kinetic_pass_double", prof["ms_double"], prof["n_double"], 2 * sw + VPHASE_FLOPS, survey_step)]
+             ("kinetic_pass_double", prof["ms_double"], prof["n_double"], 2 * sw + VPHASE_FLOPS, nlogn_step)]
     peak, peak_kind = load_peaks()
     per_kernel = {}
     for k, t, c_, fl, fs in kinds:
@@ -541,9 +541,9 @@ def gb300_arm(args):
                          "hbm_gbs": algo_bytes / avg / 1e9, "hbm_frac": algo_bytes / avg / 1e9 / peak,
                          "fp32_tflops_kernel_count": fl * batch * pts / avg / 1e12,
                          "fp32_frac_kernel_count": fl * batch * pts / avg / 1e12 / fp32_peak,
-                         "fp32_tflops_survey_count": fs * batch * pts / avg / 1e12,
-                         "fp32_frac_survey_count": fs * batch * pts / avg / 1e12 / fp32_peak,
-                         "flops_per_point_kernel_count": fl, "flops_per_point_survey_count": fs}
+                         "fp32_tflops_nlogn_count": fs * batch * pts / avg / 1e12,
+                         "fp32_frac_nlogn_count": fs * batch * pts / avg / 1e12 / fp32_peak,
+                         "flops_per_point_kernel_count": fl, "flops_per_point_nlogn_count": fs}
     name, tot_ms, cnt, _, _ = max(kinds, key=lambda k: k[1])
     dom = per_kernel[name]
     traffic = ncu_traffic(name) if args.workload == "fullscale" else None
@@ -551,9 +551,9 @@ def gb300_arm(args):
                 "traffic": traffic, "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy)",
                 # what actually limits the kinetic passes: FP32 arithmetic and
                 # instruction issue, against this GPU's measured FMA rate
-                "alu": {"achieved_tflops_survey_count": dom["fp32_tflops_survey_count"],
+                "alu": {"achieved_tflops_nlogn_count": dom["fp32_tflops_nlogn_count"],
                         "achieved_tflops_kernel_count": dom["fp32_tflops_kernel_count"],
-                        "peak_tflops": fp32_peak, "frac_survey_count": dom["fp32_frac_survey_count"],
+                        "peak_tflops": fp32_peak, "frac_nlogn_count": dom["fp32_frac_nlogn_count"],
                         "frac_kernel_count": dom["fp32_frac_kernel_count"],
                         "peak_source": "measured: hom_alu_peak FP32 FMA throughput kernel, best of 3"},
                 "fp64_peak_tflops_measured": fp64_peak,
