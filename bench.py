@@ -81,14 +81,19 @@ def load_peaks():
 
 
 def _dft_flops(n: int, tw_general: int = 14) -> int:
-    """FP32 flops of the in-register radix-2 DFT of length n (add, sub, mul = 1,
-    FMA = 2): butterflies cost 4, a trivial twiddle (1, -i) 0, a (1 -+ i)/sqrt2
-    twiddle 8 (two sums, two compensated scalings) and any other compensated
-    twiddle 14 (two products and two FMAs per component)."""
+    """FP32 flops of the in-register DFT of length n (add, sub, mul = 1, FMA =
+    2): radix 2 up to 8 points, 4 x 4 for 16; butterflies cost 4, a trivial
+    twiddle (1, -i) 0, a (1 -+ i)/sqrt2 twiddle 8 (two sums, two compensated
+    scalings) and any other compensated twiddle 14 (two products and two FMAs
+    per component)."""
     if n == 1:
         return 0
     if n == 2:
         return 4
+    if n == 16:
+        # 4 x 4 split: eight 4-point DFTs (8 complex additions each), four
+        # general and four eighth-root twiddles between the stages
+        return 8 * 16 + 4 * tw_general + 4 * 8
     tw = 0
     for k in range(1, n // 2):
         if 4 * k == n:

@@ -171,8 +171,28 @@ __device__ __forceinline__ C twiddle_const(C a, int k) {
   return cmul_hl<INV>(a, hi, lo);                                     // * (c - i s) or its conjugate
 }
 
+// 4-point DFT of (a, b, c, d) in place, forward e^{-2 pi i jk/4} or inverse
+// e^{+...} (no 1/4): the products by -+i are component swaps, so it costs
+// eight complex additions.
+template <bool INV, typename C>
+__device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
+  const C s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = csub(b, d);
+  a = cadd(s0, s1);
+  c = csub(s0, s1);
+  if (INV) {              // X1 = d0 + i d1, X3 = d0 - i d1
+    b = C{d0.x - d1.y, d0.y + d1.x};
+    d = C{d0.x + d1.y, d0.y - d1.x};
+  } else {                // X1 = d0 - i d1, X3 = d0 + i d1
+    b = C{d0.x + d1.y, d0.y - d1.x};
+    d = C{d0.x - d1.y, d0.y + d1.x};
+  }
+}
+
 // In-register DFT of length N in {1,2,4,8,16}: natural order in and out,
-// forward sum e^{-2 pi i jk/N}, inverse e^{+...} without the 1/N.
+// forward sum e^{-2 pi i jk/N}, inverse e^{+...} without the 1/N.  N = 16 is
+// split 4 x 4 (x[n2 + 4 n1] -> X[k1 + 4 k2], with W16^(n2 k1) between the
+// two 4-point stages): 4 general and 4 eighth-root twiddles, against 4 and 6
+// for the radix-2 recursion, with the same number of additions.
 template <int N, bool INV, typename C>
 __device__ __forceinline__ void dft_reg(C* v) {
   if constexpr (N == 1) {
@@ -181,8 +201,28 @@ __device__ __forceinline__ void dft_reg(C* v) {
     const C a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
+  } else if constexpr (N == 16) {
+    C t[16];   // t[4 k1 + n2]
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C a = v[n2], b = v[n2 + 4], c = v[n2 + 8], d = v[n2 + 12];
+      dft4<INV>(a, b, c, d);
+      t[n2] = a;
+      t[4 + n2] = twiddle_const<16, INV>(b, n2);
+      t[8 + n2] = twiddle_const<16, INV>(c, 2 * n2);
+      t[12 + n2] = twiddle_const<16, INV>(d, 3 * n2);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C a = t[4 * k1], b = t[4 * k1 + 1], c = t[4 * k1 + 2], d = t[4 * k1 + 3];
+      dft4<INV>(a, b, c, d);
+      v[k1] = a;
+      v[k1 + 4] = b;
+      v[k1 + 8] = c;
+      v[k1 + 12] = d;
+    }
   } else {
-    static_assert(N == 4 || N == 8 || N == 16, "register DFT length");
+    static_assert(N == 4 || N == 8, "register DFT length");
     C e[N / 2], o[N / 2];
 #pragma unroll
     for (int j = 0; j < N / 2; ++j) {
