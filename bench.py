@@ -614,9 +614,12 @@ def gb300_arm(args):
         for r in range(nrep):
             q = ctxs[r % 2]
             copy_in(q)                              # overlaps the other context's steps
-            q.step(args.inner)
             if pending is not None:
-                pending.observables()               # reads back the previous step's result
+                # read back the previous step's result before launching this
+                # one: the binding orders each call after the caller's stream,
+                # so reading it later would also wait for this step
+                pending.observables()
+            q.step(args.inner)
             pending = q
         pending.observables()
         torch.cuda.synchronize()
