@@ -426,9 +426,8 @@ __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const 
 #pragma unroll
       for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
     } else {
-      if (n2 != 0)   // W^0 = 1: no product (the index is the same across a warp)
 #pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + n2) * RS] = v[k1];
     }
@@ -466,9 +465,8 @@ __device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[(N2 * k1 + k2) * RS];
     dft_reg<N2, true>(v);
-    if (k1 != 0)   // W^0 = 1: no product (the index is the same across a warp)
 #pragma unroll
-      for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_tw<true>(v[m1], tw, m1 * k1);
+    for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_tw<true>(v[m1], tw, m1 * k1);
 #pragma unroll
     for (int m1 = 0; m1 < N2; ++m1) line[(N2 * k1 + m1) * RS] = v[m1];
   }
@@ -535,9 +533,8 @@ __device__ __forceinline__ void x_turnaround(C* sm, const C* tw, int t0, const C
 #pragma unroll
       for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
     } else {
-      if (m != 0)   // W^0 = 1: no product (the index is the same across a warp)
 #pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, m * k1);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, m * k1);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + m) * RS] = v[k1];
     }
