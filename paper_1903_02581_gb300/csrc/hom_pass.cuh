@@ -79,7 +79,7 @@ template <typename C> struct PassArgsT {
 
 // The energy weights are in the state precision: the energy terms are summed
 // per thread in that precision (a few dozen terms) and added in FP64; the
-// norm and the bunching probability are FP64 sums of exact FP64 squares.
+// norm and the bunching probability are sums of exact squares (SqSum).
 template <typename C> struct MeasureArgs {
   using R = typename Re<C>::type;
   const C* psi;
@@ -791,6 +791,38 @@ struct AccHook {
   }
 };
 
+// Sum of the exact squares |v|^2 of stored state values (the norm and the
+// bunching probability).  In FP32 each square is split exactly into its
+// rounded product and that product's error (an FMA), and the terms go into an
+// unevaluated pair of FP32 values with the two-sum error-free addition: about
+// 2^-48 relative, on the FP32 pipes, where FP64 arithmetic runs at 1/64 of
+// their rate.  In FP64 the squares are exact FP64 products of the stored
+// values and the sum a plain FP64 one.
+template <typename C> struct SqSum;
+template <> struct SqSum<double2> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double2 v) { s += cnorm2_d(v); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct SqSum<float2> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void two_sum(float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ void add(float2 v) {
+    const float px = __fmul_rn(v.x, v.x), py = __fmul_rn(v.y, v.y);
+    const float ex = fmaf(v.x, v.x, -px), ey = fmaf(v.y, v.y, -py);
+    two_sum(px);
+    two_sum(py);
+    lo = __fadd_rn(lo, __fadd_rn(ex, ey));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename T> __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -827,7 +859,7 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
   const R* v1 = a.v1 + (size_t)b * N;
   const R* v12 = a.v12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
 
-  double s_norm = 0.0, s_pb = 0.0;
+  SqSum<C> s_norm, s_pb;
   R s_pot = 0, s_coul = 0;
   for (int e = tid; e < G * N; e += NT) {
     int g, r;
@@ -837,13 +869,12 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
     const C v = base[off];
     if constexpr (!COL) {
       const int r1 = t0 + g, r2 = r;
-      const double rho = cnorm2_d(v);
       const R rr = cnorm2(v);
       const int x1 = r1 / NY, y1 = r1 % NY, x2 = r2 / NY, y2 = r2 % NY;
-      s_norm += rho;
+      s_norm.add(v);
       s_pot = fma(rr, v1[r1] + v1[r2], s_pot);
       s_coul = fma(rr, v12[(x1 - x2 + NX - 1) * (2 * NY - 1) + (y1 - y2 + NY - 1)], s_coul);
-      if ((x1 < NX / 2) == (x2 < NX / 2)) s_pb += rho;
+      if ((x1 < NX / 2) == (x2 < NX / 2)) s_pb.add(v);
     }
     sm[g * PS + (r / NY) * RS + (r % NY)] = v;
   }
@@ -854,7 +885,8 @@ measure_pass(MeasureArgs<typename Cx<T>::type> a) {
   AccHook<C, NY> hy{a.ty, (R)0, false};
   y_forward<C, NX, NY, G, NT, RS, PS>(sm, stwy, hy);
 
-  const double vals[NPART] = {s_norm, (double)s_pot, (double)s_coul, s_pb, (double)hx.acc, (double)hy.acc};
+  const double vals[NPART] = {s_norm.value(), (double)s_pot, (double)s_coul, s_pb.value(), (double)hx.acc,
+                              (double)hy.acc};
   double* out = a.partial + (size_t)tile * NPART;
 #pragma unroll
   for (int i = 0; i < NPART; ++i) {
