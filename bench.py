@@ -592,7 +592,7 @@ def gb300_arm(args):
         hview = host.numpy()
         for b in range(batch):
             H.hom_copy_state(pr.ctx, b, hview[b], to_device=False)
-        nrep = max(2, min(args.steps, 4))
+        nrep = max(2, args.steps)
         pr2 = H.Propagator(w, device=f"cuda:{local}", init=False)
         if args.pin:
             H.hom_autotune_set(pr2.ctx, *[int(v) for v in args.pin.split(",")])
