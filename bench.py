@@ -82,7 +82,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def _dft_flops(n: int, tw_general: int = 14) -> int:
+def _dft_flops(n: int, tw_general: int = 14, split44: bool = False) -> int:
     """FP32 flops of the in-register DFT of length n (add, sub, mul = 1, FMA =
     2): radix 2 up to 8 points, 4 x 4 for 16; butterflies cost 4, a trivial
     twiddle (1, -i) 0, a (1 -+ i)/sqrt2 twiddle 8 (two sums, two compensated
@@ -92,9 +92,9 @@ def _dft_flops(n: int, tw_general: int = 14) -> int:
         return 0
     if n == 2:
         return 4
-    if n == 16:
-        # 4 x 4 split: eight 4-point DFTs (8 complex additions each), four
-        # general and four eighth-root twiddles between the stages
+    if n == 16 and split44:
+        # 4 x 4 split (the x axis of the 256 x 64 grid): eight 4-point DFTs
+        # (8 complex additions each), four general and four eighth-root twiddles
         return 8 * 16 + 4 * tw_general + 4 * 8
     tw = 0
     for k in range(1, n // 2):
@@ -116,14 +116,15 @@ def sandwich_flops(nx: int, ny: int, fp64: bool = False) -> float:
     scale (2).  In FP64 a general twiddle is a plain complex product (6): the
     low parts of the compensated pairs are FP32-only."""
     tw, ph = (6.0 if fp64 else 14.0), 8.0
-    dft = (lambda n: _dft_flops(n, 6)) if fp64 else _dft_flops
+    dft = (lambda n, s44=False: _dft_flops(n, 6, s44)) if fp64 else (lambda n, s44=False: _dft_flops(n, 14, s44))
+    x44 = nx == 256                  # the kernels split the x axis' 16-point DFTs 4 x 4 there
     f = 0.0
     n1, n2 = _split(nx)
     if n2 == 1:
-        f += dft(nx) / nx + ph + dft(nx) / nx
+        f += dft(nx, x44) / nx + ph + dft(nx, x44) / nx
     else:
-        f += dft(n1) / n1 + tw * (n1 - 1) / n1 + dft(n2) / n2 + ph       # forward x, T_x/2
-        f += dft(n2) / n2 + tw * (n2 - 1) / n2 + dft(n1) / n1            # inverse x
+        f += dft(n1, x44) / n1 + tw * (n1 - 1) / n1 + dft(n2, x44) / n2 + ph       # forward x, T_x/2
+        f += dft(n2, x44) / n2 + tw * (n2 - 1) / n2 + dft(n1, x44) / n1            # inverse x
     m1, m2 = _split(ny)
     if m2 == 1:
         f += 2 * dft(ny) / ny + ph + 2 + ph

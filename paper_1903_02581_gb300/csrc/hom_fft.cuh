@@ -189,11 +189,12 @@ __device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
 }
 
 // In-register DFT of length N in {1,2,4,8,16}: natural order in and out,
-// forward sum e^{-2 pi i jk/N}, inverse e^{+...} without the 1/N.  N = 16 is
-// split 4 x 4 (x[n2 + 4 n1] -> X[k1 + 4 k2], with W16^(n2 k1) between the
-// two 4-point stages): 4 general and 4 eighth-root twiddles, against 4 and 6
-// for the radix-2 recursion, with the same number of additions.
-template <int N, bool INV, typename C>
+// forward sum e^{-2 pi i jk/N}, inverse e^{+...} without the 1/N.  With S44,
+// N = 16 is split 4 x 4 (x[n2 + 4 n1] -> X[k1 + 4 k2], with W16^(n2 k1)
+// between the two 4-point stages): 4 general and 4 eighth-root twiddles,
+// against 4 and 6 for the radix-2 recursion, with the same number of
+// additions, but more values live at once (see kX44 in hom_pass.cuh).
+template <int N, bool INV, bool S44 = false, typename C>
 __device__ __forceinline__ void dft_reg(C* v) {
   if constexpr (N == 1) {
     return;
@@ -201,7 +202,7 @@ __device__ __forceinline__ void dft_reg(C* v) {
     const C a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
-  } else if constexpr (N == 16) {
+  } else if constexpr (N == 16 && S44) {
     C t[16];   // t[4 k1 + n2]
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) {
@@ -222,7 +223,7 @@ __device__ __forceinline__ void dft_reg(C* v) {
       v[k1 + 12] = d;
     }
   } else {
-    static_assert(N == 4 || N == 8, "register DFT length");
+    static_assert(N == 4 || N == 8 || N == 16, "register DFT length");
     C e[N / 2], o[N / 2];
 #pragma unroll
     for (int j = 0; j < N / 2; ++j) {

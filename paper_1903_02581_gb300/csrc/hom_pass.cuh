@@ -139,6 +139,13 @@ template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   static constexpr size_t SMEM_ALL = TMA_STORE ? STAGE_OFF + (size_t)STAGE * sizeof(C) + 128 : SMEM;
 };
 
+// The 16-point DFTs of the x axis are split 4 x 4 (fewer twiddles, more live
+// values: see dft_reg) only where the x axis is 256 long: there it shortened
+// the double pass by 2.3 %, while on the 128-long axis of the batched grid it
+// slowed the transposing pass by 7.6 %.  Every kernel of a grid uses the same
+// choice, so the step strategies stay bitwise identical.
+template <int NX> constexpr bool kX44 = NX == 256;
+
 // ---------------------------------------------------------------------------
 // Line transforms over the shared-memory planes.  An x-line is the column of
 // one (g, y); a y-line is the row of one (g, x position).
@@ -162,7 +169,7 @@ __device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
       C v[NX];
 #pragma unroll
       for (int x = 0; x < NX; ++x) v[x] = line[x * RS];
-      dft_reg<NX, false>(v);
+      dft_reg<NX, false, kX44<NX>>(v);
 #pragma unroll
       for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
     }
@@ -174,7 +181,7 @@ __device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
       C v[N1];
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = line[(N2 * n1 + n2) * RS];
-      dft_reg<N1, false>(v);
+      dft_reg<N1, false, kX44<NX>>(v);
 #pragma unroll
       for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul_tw<false>(v[k1], tw, n2 * k1);
 #pragma unroll
@@ -187,7 +194,7 @@ __device__ __forceinline__ void x_forward(C* sm, const C* tw, Hook& hook) {
       C v[N2];
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) v[n2] = line[(N2 * k1 + n2) * RS];
-      dft_reg<N2, false>(v);
+      dft_reg<N2, false, kX44<NX>>(v);
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) line[(N2 * k1 + k2) * RS] = hook(N2 * k1 + k2, y, v[k2]);
     }
@@ -420,7 +427,7 @@ __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const 
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = apply_delta(v[n1], d[n1]);
     }
-    dft_reg<N1, false>(v);
+    dft_reg<N1, false, kX44<NX>>(v);
     C* line = sm + g * PS + y;
     if constexpr (N2 == 1) {
 #pragma unroll
@@ -446,7 +453,7 @@ __device__ __forceinline__ void x_forward_second(C* sm, Hook& hook) {
     C v[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) v[n2] = line[(N2 * k1 + n2) * RS];
-    dft_reg<N2, false>(v);
+    dft_reg<N2, false, kX44<NX>>(v);
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) line[(N2 * k1 + k2) * RS] = hook(N2 * k1 + k2, y, v[k2]);
   }
@@ -464,7 +471,7 @@ __device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
     C v[N2];
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) v[k2] = line[(N2 * k1 + k2) * RS];
-    dft_reg<N2, true>(v);
+    dft_reg<N2, true, kX44<NX>>(v);
 #pragma unroll
     for (int m1 = 1; m1 < N2; ++m1) v[m1] = cmul_tw<true>(v[m1], tw, m1 * k1);
 #pragma unroll
@@ -491,7 +498,7 @@ __device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__
     C v[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[(N2 * k1 + m1) * RS];
-    dft_reg<N1, true>(v);
+    dft_reg<N1, true, kX44<NX>>(v);
     if (apply_v) {
 #pragma unroll
       for (int m2 = 0; m2 < N1; ++m2)
@@ -522,13 +529,13 @@ __device__ __forceinline__ void x_turnaround(C* sm, const C* tw, int t0, const C
     C v[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[(N2 * k1 + m) * RS];
-    dft_reg<N1, true>(v);
+    dft_reg<N1, true, kX44<NX>>(v);
     C d[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) d[n1] = vphase_delta<C, NX, NY>(p1, p12, t0 + g, (N2 * n1 + m) * NY + y);
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = apply_delta(v[n1], d[n1]);
-    dft_reg<N1, false>(v);
+    dft_reg<N1, false, kX44<NX>>(v);
     if constexpr (N2 == 1) {
 #pragma unroll
       for (int k = 0; k < NX; ++k) line[k * RS] = hook(k, y, v[k]);
@@ -562,7 +569,7 @@ __device__ __forceinline__ void x_inverse_cluster_store(const C* sm, C* __restri
     C v[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(N2 * k1 + m1) * RS];
-    dft_reg<N1, true>(v);
+    dft_reg<N1, true, kX44<NX>>(v);
     if (apply_v) {
 #pragma unroll
       for (int m2 = 0; m2 < N1; ++m2)
@@ -669,7 +676,7 @@ __device__ __forceinline__ void x_inverse_cluster_store_tma(const C* sm, C* stag
       C v[N1];
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(N2 * k1 + m1) * RS];
-      dft_reg<N1, true>(v);
+      dft_reg<N1, true, kX44<NX>>(v);
       if (apply_v) {
 #pragma unroll
         for (int m2 = 0; m2 < N1; ++m2)
