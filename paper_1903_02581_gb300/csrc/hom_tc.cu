@@ -257,7 +257,11 @@ extern "C" hom_status hom_ysandwich_tc(const float* d_in, float* d_out, int32_t 
   if (cudaFuncSetAttribute(ysandwich_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) != cudaSuccess)
     return HOM_ERR_CUDA;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HOM_ERR_CUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess) return HOM_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return HOM_ERR_CUDA;
+  }
   hom_status s = HOM_OK;
   float total = 0.f;
   for (int r = 0; r <= nrep && s == HOM_OK; ++r) {   // launch 0 is a warm-up
