@@ -759,9 +759,12 @@ kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
 // through shared memory (row stride T + 1: conflict-free column reads), rows
 // read and written as contiguous T-element segments, both with streaming
 // (evict-first) cache hints: every byte is touched once.  Used between
-// in-place passes by step strategies 1 and 2 (see step_sequence).
+// in-place passes by step strategies 1 and 2 (see step_sequence).  The launch
+// bound keeps four CTAs resident per SM (64 registers, no spills): the copy
+// waits on DRAM latency, and four CTAs hide it where the two that 124
+// registers allowed did not.
 template <typename C, int T>
-__global__ void __launch_bounds__(256) transpose_state(const C* __restrict__ src, C* __restrict__ dst, int n,
+__global__ void __launch_bounds__(256, 4) transpose_state(const C* __restrict__ src, C* __restrict__ dst, int n,
                                                        int batch) {
   __shared__ C tile[T][T + 1];
   constexpr int ROWS = 256 / T;
