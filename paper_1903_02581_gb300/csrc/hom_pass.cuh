@@ -129,6 +129,12 @@ template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   // kernel uses the other count
   static constexpr int NT0 = (sizeof(C) == 8 && G * N >= 8192) ? 512 : 256;
   static constexpr int NT = (V == 1 && CL0 == 1) ? (NT0 == 512 ? 256 : 512) : NT0;
+  // x stages owned by XG thread groups (see x_item): on the 256x64 complex64
+  // grid, where it shortened the double pass by 6 % (groups of one plane's
+  // columns drift apart between the y sandwiches, so one group's shared-memory
+  // and load phases overlap another's arithmetic).  Elsewhere 1: every stage
+  // ends with a CTA barrier.
+  static constexpr int XG = (sizeof(C) == 8 && NX == 256 && NY == 64 && G == 1) ? 4 : 1;
   // clustered complex64 transposing pass: its stores go through the tensor
   // memory accelerator from two staging buffers of N1 tiles of ny rows x CL*G
   // columns (see x_inverse_cluster_store_tma)
@@ -150,6 +156,42 @@ template <int NX> constexpr bool kX44 = NX == 256;
 // Line transforms over the shared-memory planes.  An x-line is the column of
 // one (g, y); a y-line is the row of one (g, x position).
 // ---------------------------------------------------------------------------
+
+// Item (g, y, sub) of an x stage: the x-line (column) of plane g at y, and the
+// sub-line index (n2, k1 or m) of the stage.  XG == 1: lanes run over y, then
+// sub, then g.  XG > 1 (one plane per CTA): thread group q = tid / (NT/XG)
+// owns the columns [q*CPG, (q+1)*CPG), CPG = NY/XG, with lanes still running
+// over consecutive y (whole 128-byte segments in global and shared memory),
+// so each column's stages stay inside one group and only that group needs to
+// synchronise between them (group_sync).  Any bijection of items onto threads
+// gives the same bits: an item's arithmetic does not depend on its thread.
+template <int NT, int NY, int G, int NSUB, int XG>
+__device__ __forceinline__ void x_item(int it, int& g, int& y, int& sub) {
+  if constexpr (XG == 1) {
+    y = it % NY;
+    sub = (it / NY) % NSUB;
+    g = it / (NY * NSUB);
+  } else {
+    constexpr int TPG = NT / XG, CPG = NY / XG;
+    static_assert(G == 1 && NY % XG == 0 && NT % (32 * XG) == 0 && TPG % CPG == 0 && NSUB % (TPG / CPG) == 0,
+                  "x-stage thread groups");
+    const int t = it % NT, q = t % TPG;
+    g = 0;
+    y = (t / TPG) * CPG + q % CPG;
+    sub = q / CPG + (TPG / CPG) * (it / NT);
+  }
+}
+
+// Barrier over the thread group of x_item (named barrier 1 + group; barrier 0
+// is __syncthreads), or over the CTA when XG == 1.
+template <int NT, int XG>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (XG == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / (NT / XG)), "r"(NT / XG) : "memory");
+  }
+}
 
 struct NoHook {
   template <typename C> __device__ __forceinline__ C operator()(int, int, C v) const { return v; }
@@ -408,7 +450,7 @@ __device__ __forceinline__ size_t global_offset(int t0, int g, int x, int y) {
 // t0 + g and the element index may be either particle's), transforms, and
 // writes shared memory.  With nx <= 16 this
 // is the whole forward x transform, followed by the T_x/2 hook.
-template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL, class Hook>
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL, int XG, class Hook>
 __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const C* __restrict__ base, int t0,
                                                       const C* __restrict__ p1, const C* __restrict__ p12,
                                                       bool apply_v, Hook& hook) {
@@ -416,7 +458,8 @@ __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const 
   constexpr int N1 = S::N1, N2 = S::N2;
   for (int it = threadIdx.x; it < G * NY * N2; it += NT) {
     int g, y, n2;
-    decode_item<COL, NY, G, N2>(it, g, y, n2);
+    if constexpr (COL) decode_item<COL, NY, G, N2>(it, g, y, n2);
+    else x_item<NT, NY, G, N2, XG>(it, g, y, n2);
     C v[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = __ldcs(base + global_offset<COL, NX, NY>(t0, g, N2 * n1 + n2, y));
@@ -439,16 +482,19 @@ __device__ __forceinline__ void x_forward_from_global(C* sm, const C* tw, const 
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + n2) * RS] = v[k1];
     }
   }
-  __syncthreads();
+  // the second x stage reads only this group's columns
+  if constexpr (N2 > 1 && !COL) group_sync<NT, XG>();
+  else __syncthreads();
 }
 
 // Second forward x stage (shared memory only, nx > 16), hook on every output.
-template <typename C, int NX, int NY, int G, int NT, int RS, int PS, class Hook>
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, int XG, class Hook>
 __device__ __forceinline__ void x_forward_second(C* sm, Hook& hook) {
   using S = Split<NX>;
   constexpr int N1 = S::N1, N2 = S::N2;
   for (int it = threadIdx.x; it < G * NY * N1; it += NT) {
-    const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
+    int g, y, k1;
+    x_item<NT, NY, G, N1, XG>(it, g, y, k1);
     C* line = sm + g * PS + y;
     C v[N2];
 #pragma unroll
@@ -460,13 +506,15 @@ __device__ __forceinline__ void x_forward_second(C* sm, Hook& hook) {
   __syncthreads();
 }
 
-// First inverse x stage (shared memory only, nx > 16).
-template <typename C, int NX, int NY, int G, int NT, int RS, int PS>
+// First inverse x stage (shared memory only, nx > 16).  GROUP: the next stage
+// reads only this group's columns (x_item), so a group barrier ends it.
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, int XG, bool GROUP>
 __device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
   using S = Split<NX>;
   constexpr int N1 = S::N1, N2 = S::N2;
   for (int it = threadIdx.x; it < G * NY * N1; it += NT) {
-    const int y = it % NY, k1 = (it / NY) % N1, g = it / (NY * N1);
+    int g, y, k1;
+    x_item<NT, NY, G, N1, XG>(it, g, y, k1);
     C* line = sm + g * PS + y;
     C v[N2];
 #pragma unroll
@@ -477,7 +525,8 @@ __device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
 #pragma unroll
     for (int m1 = 0; m1 < N2; ++m1) line[(N2 * k1 + m1) * RS] = v[m1];
   }
-  __syncthreads();
+  if constexpr (GROUP) group_sync<NT, XG>();
+  else __syncthreads();
 }
 
 // Last inverse x stage written straight to global memory with streaming
@@ -485,7 +534,7 @@ __device__ __forceinline__ void x_inverse_first(C* sm, const C* tw) {
 // potential phase if asked.
 // COL = false writes the planes back as rows; COL = true writes them
 // transposed (element (x, y) of plane t0 + g to row x*ny + y, column t0 + g).
-template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL>
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, bool COL, int XG>
 __device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__ base, int t0,
                                                     const C* __restrict__ p1, const C* __restrict__ p12,
                                                     bool apply_v) {
@@ -493,7 +542,8 @@ __device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__
   constexpr int N1 = S::N1, N2 = S::N2;
   for (int it = threadIdx.x; it < G * NY * N2; it += NT) {
     int g, y, m1;
-    decode_item<COL, NY, G, N2>(it, g, y, m1);
+    if constexpr (COL) decode_item<COL, NY, G, N2>(it, g, y, m1);
+    else x_item<NT, NY, G, N2, XG>(it, g, y, m1);
     const C* line = sm + g * PS + y;
     C v[N1];
 #pragma unroll
@@ -517,14 +567,14 @@ __device__ __forceinline__ void x_inverse_to_global(const C* sm, C* __restrict__
 // forward again and writes back the shared-memory positions it read.  With
 // nx <= 16 this is the whole inverse and forward x transform, followed by the
 // T_x/2 hook.
-template <typename C, int NX, int NY, int G, int NT, int RS, int PS, class Hook>
+template <typename C, int NX, int NY, int G, int NT, int RS, int PS, int XG, class Hook>
 __device__ __forceinline__ void x_turnaround(C* sm, const C* tw, int t0, const C* __restrict__ p1,
                                              const C* __restrict__ p12, Hook& hook) {
   using S = Split<NX>;
   constexpr int N1 = S::N1, N2 = S::N2;
   for (int it = threadIdx.x; it < G * NY * N2; it += NT) {
     int g, y, m;
-    decode_item<false, NY, G, N2>(it, g, y, m);
+    x_item<NT, NY, G, N2, XG>(it, g, y, m);
     C* line = sm + g * PS + y;
     C v[N1];
 #pragma unroll
@@ -546,7 +596,10 @@ __device__ __forceinline__ void x_turnaround(C* sm, const C* tw, int t0, const C
       for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + m) * RS] = v[k1];
     }
   }
-  __syncthreads();
+  // the second x stage reads only this group's columns; with nx <= 16 the y
+  // sandwich comes next
+  if constexpr (N2 > 1) group_sync<NT, XG>();
+  else __syncthreads();
 }
 
 // Transposed store of a cluster of CL CTAs holding W = CL*G adjacent planes:
@@ -615,18 +668,19 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
     prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
   }
   __syncthreads();                               // twiddles in shared memory
-  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false>(sm, stwx, base, t0, p1, p12, a.v_load != 0, qa);
-  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
+  constexpr int XG = Gm::XG;
+  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, stwx, base, t0, p1, p12, a.v_load != 0, qa);
+  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
   y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
-  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, true>(sm, stwx);
   if constexpr (TWICE) {
-    x_turnaround<C, NX, NY, G, NT, RS, PS>(sm, stwx, t0, a.p1m + (size_t)b * N,
-                                           a.p12m + (size_t)b * (2 * NX - 1) * (2 * NY - 1), qa);
-    if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
+    x_turnaround<C, NX, NY, G, NT, RS, PS, XG>(sm, stwx, t0, a.p1m + (size_t)b * N,
+                                               a.p12m + (size_t)b * (2 * NX - 1) * (2 * NY - 1), qa);
+    if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
     y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
-    if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+    if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, true>(sm, stwx);
   }
-  x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false>(sm, base, t0, p1, p12, a.v_store != 0);
+  x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, base, t0, p1, p12, a.v_store != 0);
 }
 
 // One kinetic sandwich of the particle whose plane is a row of src, written
@@ -728,13 +782,15 @@ kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
     prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
   }
   __syncthreads();                               // twiddles in shared memory
-  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false>(sm, stwx, src, t0, p1, p12, a.v_load != 0, qa);
-  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS>(sm, qa);
+  constexpr int XG = Gm::XG;
+  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, stwx, src, t0, p1, p12, a.v_load != 0, qa);
+  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
   y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
-  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS>(sm, stwx);
+  // the transposed stores below read every column: a CTA barrier
+  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, false>(sm, stwx);
   if constexpr (CL == 1) {
     // G >= 4 adjacent rows: the transposed store writes G*8-byte segments
-    x_inverse_to_global<C, NX, NY, G, NT, RS, PS, true>(sm, dst, t0, p1, p12, a.v_store != 0);
+    x_inverse_to_global<C, NX, NY, G, NT, RS, PS, true, XG>(sm, dst, t0, p1, p12, a.v_store != 0);
   } else {
     // a cluster of CL CTAs holds CL*G adjacent rows: each CTA stores its share
     // of all of them as 32-byte segments, read through distributed shared memory
