@@ -54,7 +54,8 @@ template <typename C> struct PassArgs {
   const C* p12m;
   int v_load;          // apply the potential phase when loading
   int v_store;         // apply the potential phase when storing
-  int pref_ahead;      // prefetch into L2 the tile this many CTAs ahead (0: off)
+  int pref_ahead;      // nonzero: prefetch into L2 the tile a CTA takes next
+  int ntiles;          // tiles of the launch: CTA c takes tiles c, c + gridDim.x, ...
 };
 
 // Transposing pass: reads G contiguous rows of src ([n][n] per simulation,
@@ -638,6 +639,12 @@ __device__ __forceinline__ void x_inverse_cluster_store(const C* sm, C* __restri
 // TWICE: two sandwiches of the same particle with the potential phase of a
 // full step between them (the end of one Strang step and the start of the
 // next, when the state is not transposed in between).
+// Persistent: the launch holds the CTAs that fit on the device at once, and
+// each walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The twiddles
+// are staged once per CTA, the next tile is prefetched into L2 while the
+// current one is transformed, and with x-stage groups (XG > 1) a group goes
+// from storing its columns of one tile to loading them for the next without
+// waiting for the other groups.
 template <typename T, int NX, int NY, int V, bool TWICE>
 __global__ void __launch_bounds__(Geo<T, NX, NY, false, V>::NT)
 kinetic_pass(PassArgs<typename Cx<T>::type> a) {
@@ -645,6 +652,7 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   using C = typename Cx<T>::type;
   constexpr int N = Gm::N, G = Gm::G, NT = Gm::NT, RS = Gm::RS, PS = Gm::PS;
   constexpr int N2X = Split<NX>::N2;
+  constexpr int XG = Gm::XG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   C* stwx = sm + Gm::TWOFF;
@@ -652,35 +660,38 @@ kinetic_pass(PassArgs<typename Cx<T>::type> a) {
   const int tid = threadIdx.x;
   for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
   for (int i = tid; i < 2 * NY; i += NT) stwy[i] = a.twy[i];
-
-  const int tile = blockIdx.x;
-  const int b = tile / Gm::TILES_PER_SIM;
-  const int t0 = (tile % Gm::TILES_PER_SIM) * G;
-  C* base = a.psi + (size_t)b * N * N;
-  const C* p1 = a.p1 + (size_t)b * N;
-  const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
   QHook<C, NY> qa{a.qa};
-
-  // start the HBM read of the tile one wave later into L2
-  if (tid == 0 && a.pref_ahead > 0 && tile + a.pref_ahead < (int)gridDim.x) {
-    const int nt = tile + a.pref_ahead;
-    const C* p = a.psi + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
-    prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
-  }
   __syncthreads();                               // twiddles in shared memory
-  constexpr int XG = Gm::XG;
-  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, stwx, base, t0, p1, p12, a.v_load != 0, qa);
-  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
-  y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
-  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, true>(sm, stwx);
-  if constexpr (TWICE) {
-    x_turnaround<C, NX, NY, G, NT, RS, PS, XG>(sm, stwx, t0, a.p1m + (size_t)b * N,
-                                               a.p12m + (size_t)b * (2 * NX - 1) * (2 * NY - 1), qa);
+
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int b = tile / Gm::TILES_PER_SIM;
+    const int t0 = (tile % Gm::TILES_PER_SIM) * G;
+    C* base = a.psi + (size_t)b * N * N;
+    const C* p1 = a.p1 + (size_t)b * N;
+    const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
+
+    // start the HBM read of this CTA's next tile into L2
+    const int nt = tile + (int)gridDim.x;
+    if (tid == 0 && a.pref_ahead > 0 && nt < a.ntiles) {
+      const C* p = a.psi + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
+      prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
+    }
+    x_forward_from_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, stwx, base, t0, p1, p12, a.v_load != 0, qa);
     if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
     y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
     if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, true>(sm, stwx);
+    if constexpr (TWICE) {
+      x_turnaround<C, NX, NY, G, NT, RS, PS, XG>(sm, stwx, t0, a.p1m + (size_t)b * N,
+                                                 a.p12m + (size_t)b * (2 * NX - 1) * (2 * NY - 1), qa);
+      if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
+      y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
+      if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, true>(sm, stwx);
+    }
+    x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, base, t0, p1, p12, a.v_store != 0);
+    // the next tile's first stage overwrites the shared memory just read
+    // (only this group's columns when XG > 1)
+    group_sync<NT, XG>();
   }
-  x_inverse_to_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, base, t0, p1, p12, a.v_store != 0);
 }
 
 // One kinetic sandwich of the particle whose plane is a row of src, written
