@@ -130,12 +130,20 @@ template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   // kernel uses the other count
   static constexpr int NT0 = (sizeof(C) == 8 && G * N >= 8192) ? 512 : 256;
   static constexpr int NT = (V == 1 && CL0 == 1) ? (NT0 == 512 ? 256 : 512) : NT0;
-  // x stages owned by XG thread groups (see x_item): on the 256x64 complex64
-  // grid, where it shortened the double pass by 6 % (groups of one plane's
-  // columns drift apart between the y sandwiches, so one group's shared-memory
-  // and load phases overlap another's arithmetic).  Elsewhere 1: every stage
-  // ends with a CTA barrier.
-  static constexpr int XG = (sizeof(C) == 8 && NX == 256 && NY == 64 && G == 1) ? 4 : 1;
+  // x stages owned by XG thread groups of 16 columns each (see x_item), where
+  // the thread counts divide evenly and the grid was measured to gain: groups
+  // drift apart between the y sandwiches, so one group's shared-memory and
+  // load phases overlap another's arithmetic (the 256x64 double pass: 6 %
+  // shorter; the 128x32 in-place pass: 2 %; the 4-plane transposing pass of
+  // the 128x32 grid ran 9 % slower with them).  Elsewhere 1: every stage ends
+  // with a CTA barrier.
+  static constexpr int XGC = G * NY / 16;
+  static constexpr int XTPG = XGC > 0 ? NT / XGC : 0;
+  static constexpr bool XOK = sizeof(C) == 8 && XGC > 1 && XGC <= 15 && NT % (32 * XGC) == 0 && XTPG % 16 == 0 &&
+                              Split<NX>::N2 > 1 && Split<NX>::N1 % (XTPG / 16) == 0 &&
+                              Split<NX>::N2 % (XTPG / 16) == 0;
+  static constexpr bool XMEASURED = (NX == 256 && NY == 64) || (NX == 128 && NY == 32 && !COL);
+  static constexpr int XG = (XOK && XMEASURED) ? XGC : 1;
   // clustered complex64 transposing pass: its stores go through the tensor
   // memory accelerator from two staging buffers of N1 tiles of ny rows x CL*G
   // columns (see x_inverse_cluster_store_tma)
@@ -160,10 +168,10 @@ template <int NX> constexpr bool kX44 = NX == 256;
 
 // Item (g, y, sub) of an x stage: the x-line (column) of plane g at y, and the
 // sub-line index (n2, k1 or m) of the stage.  XG == 1: lanes run over y, then
-// sub, then g.  XG > 1 (one plane per CTA): thread group q = tid / (NT/XG)
-// owns the columns [q*CPG, (q+1)*CPG), CPG = NY/XG, with lanes still running
-// over consecutive y (whole 128-byte segments in global and shared memory),
-// so each column's stages stay inside one group and only that group needs to
+// sub, then g.  XG > 1: thread group q = tid / (NT/XG) owns the columns
+// c = g*NY + y in [q*CPG, (q+1)*CPG), CPG = G*NY/XG (16: a 128-byte row
+// segment of complex64), with lanes still running over consecutive y, so each
+// column's stages stay inside one group and only that group needs to
 // synchronise between them (group_sync).  Any bijection of items onto threads
 // gives the same bits: an item's arithmetic does not depend on its thread.
 template <int NT, int NY, int G, int NSUB, int XG>
@@ -173,12 +181,14 @@ __device__ __forceinline__ void x_item(int it, int& g, int& y, int& sub) {
     sub = (it / NY) % NSUB;
     g = it / (NY * NSUB);
   } else {
-    constexpr int TPG = NT / XG, CPG = NY / XG;
-    static_assert(G == 1 && NY % XG == 0 && NT % (32 * XG) == 0 && TPG % CPG == 0 && NSUB % (TPG / CPG) == 0,
+    constexpr int TPG = NT / XG, CPG = G * NY / XG;
+    static_assert((G * NY) % XG == 0 && NY % CPG == 0 && NT % (32 * XG) == 0 && TPG % CPG == 0 &&
+                      NSUB % (TPG / CPG) == 0,
                   "x-stage thread groups");
     const int t = it % NT, q = t % TPG;
-    g = 0;
-    y = (t / TPG) * CPG + q % CPG;
+    const int c = (t / TPG) * CPG + q % CPG;
+    g = c / NY;
+    y = c % NY;
     sub = q / CPG + (TPG / CPG) * (it / NT);
   }
 }
