@@ -51,7 +51,9 @@ CHOICES = list(itertools.product((0, 1), (0, 1), (0, 1, 2)))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 16), (64, 32), (128, 16), (16, 64)])
+# (128, 32): the grid of the batched sweep, whose in-place pass runs its x
+# stages in column groups while its transposing pass does not
+@pytest.mark.parametrize("nx,ny", [(16, 16), (32, 16), (64, 32), (128, 16), (16, 64), (128, 32)])
 @pytest.mark.parametrize("nsteps", [1, 2, 5])
 def test_choices_bitwise_identical(prec, nx, ny, nsteps):
     w = small_w(nx, ny, prec)
@@ -74,6 +76,32 @@ def test_choices_bitwise_identical(prec, nx, ny, nsteps):
         ref = O.propagate(s0, m, nsteps)
         err = np.max(np.abs(base.astype(np.complex128) - ref)) / np.linalg.norm(ref.ravel())
         assert err <= (1e-11 if prec == "c128" else 2e-6)
+
+
+def test_choices_bitwise_identical_fullscale():
+    """The full-scale grid (256x64 per electron, complex64, a 2 GiB state),
+    where every kinetic pass runs its x stages in column groups and the
+    in-place pass is persistent: three steps under every strategy and variant
+    give the same bits.  The states are compared on the device."""
+    import torch
+
+    w = W.fullscale()
+    ref = None
+    for ch in CHOICES:
+        pr = H().Propagator(w)
+        H().hom_autotune_set(pr.ctx, *ch)
+        pr.step(3)
+        assert H().hom_autotune_info(pr.ctx)["strategy"] == ch[2]
+        bits = torch.view_as_real(pr.state).view(torch.int32)
+        if ref is None:
+            ref = bits.clone()
+            assert bool(torch.isfinite(torch.view_as_real(pr.state)).all())
+        else:
+            assert torch.equal(bits, ref), ch
+        pr.close()
+        del pr, bits
+    del ref
+    torch.cuda.empty_cache()
 
 
 def test_strategy_one_batched_profile_counts():
