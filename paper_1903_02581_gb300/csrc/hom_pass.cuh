@@ -139,9 +139,9 @@ template <typename T, int NX, int NY, bool COL, int V = 0> struct Geo {
   // with a CTA barrier.
   static constexpr int XGC = G * NY / 16;
   static constexpr int XTPG = XGC > 0 ? NT / XGC : 0;
+  static constexpr int XSUB = XTPG >= 16 ? XTPG / 16 : 1;   // sub-line indices a group covers at once
   static constexpr bool XOK = sizeof(C) == 8 && XGC > 1 && XGC <= 15 && NT % (32 * XGC) == 0 && XTPG % 16 == 0 &&
-                              Split<NX>::N2 > 1 && Split<NX>::N1 % (XTPG / 16) == 0 &&
-                              Split<NX>::N2 % (XTPG / 16) == 0;
+                              Split<NX>::N2 > 1 && Split<NX>::N1 % XSUB == 0 && Split<NX>::N2 % XSUB == 0;
   static constexpr bool XMEASURED = (NX == 256 && NY == 64) || (NX == 128 && NY == 32 && !COL);
   static constexpr int XG = (XOK && XMEASURED) ? XGC : 1;
   // clustered complex64 transposing pass: its stores go through the tensor

@@ -91,6 +91,30 @@ def fullscale2():
             "rows": rows, "obs": obs}
 
 
+def fullscale_lie2():
+    """Two steps of the paper's printed first-order product (Eq. evoloperat,
+    the Lie order: T_x, T_y, then V, each over a full step) on the full-scale
+    workload, from the oracle's own initial state."""
+    w = W.fullscale(sigma=2.0)
+    w["split"] = "lie"
+    sim = w["sims"][0]
+    m = A.model_for(w, sim)
+    t0 = time.time()
+    psi = A.initial_state(w, sim)
+    V = O.v_total(m)
+    for i in range(2):
+        psi = O.lie_step(psi, m, vtot=V)
+        print(f"step {i + 1}: {time.time() - t0:.0f}s", flush=True)
+    del V
+    obs = {"2": O.observables(psi, m)}
+    ny = w["ny"]
+    rows, vals = sampled_rows(psi, 4, 5, extra=(0 * ny + 37, (w["nx"] - 1) * ny + 37, (w["nx"] // 2) * ny + 37))
+    print(f"done: {time.time() - t0:.0f}s, P_b = {obs['2']['p_bunch']:.15f}", flush=True)
+    np.savez(os.path.join(HERE, "fullscale_lie2_oracle.npz"), rows=np.array(rows), psi_rows=vals)
+    return {"workload": "fullscale", "split": "lie", "sigma": 2.0, "nx": w["nx"], "ny": w["ny"], "dt": w["dt"],
+            "nsteps": 2, "rows": rows, "obs": obs}
+
+
 def batched():
     """Simulations 0 (Coulomb off) and 31 (Coulomb on) of the batched sweep."""
     w = W.batched()
@@ -123,6 +147,6 @@ def batched():
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "sweep32"
-    res = {"sweep32": sweep32, "fullscale2": fullscale2, "batched": batched}[which]()
+    res = {"sweep32": sweep32, "fullscale2": fullscale2, "fullscale_lie2": fullscale_lie2, "batched": batched}[which]()
     with open(os.path.join(HERE, f"{which}_oracle.json"), "w") as f:
         json.dump(res, f, indent=1)
