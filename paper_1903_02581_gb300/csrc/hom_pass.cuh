@@ -76,6 +76,7 @@ template <typename C> struct PassArgsT {
   int v_load;          // apply the potential phase when loading
   int v_store;         // apply the potential phase when storing
   int pref_ahead;      // prefetch into L2 the tile this many CTAs ahead (0: off)
+  int ntiles;          // tiles of the launch (without a cluster the pass is persistent)
 };
 
 // The energy weights are in the state precision: the energy terms are summed
@@ -788,47 +789,55 @@ kinetic_pass_t(const __grid_constant__ PassArgsT<typename Cx<T>::type> a) {
   for (int i = tid; i < 2 * NX; i += NT) stwx[i] = a.twx[i];
   for (int i = tid; i < 2 * NY; i += NT) stwy[i] = a.twy[i];
 
-  const int tile = blockIdx.x;
-  const int b = tile / Gm::TILES_PER_SIM;
-  const int t0 = (tile % Gm::TILES_PER_SIM) * G;
-  const C* src = a.src + (size_t)b * N * N;
-  C* dst = a.dst + (size_t)b * N * N;
-  const C* p1 = a.p1 + (size_t)b * N;
-  const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
   QHook<C, NY> qa{a.qa};
-
-  if (tid == 0 && a.pref_ahead > 0 && tile + a.pref_ahead < (int)gridDim.x) {
-    const int nt = tile + a.pref_ahead;
-    const C* p = a.src + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
-    prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
-  }
-  __syncthreads();                               // twiddles in shared memory
   constexpr int XG = Gm::XG;
-  x_forward_from_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, stwx, src, t0, p1, p12, a.v_load != 0, qa);
-  if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
-  y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
-  // the transposed stores below read every column: a CTA barrier
-  if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, false>(sm, stwx);
-  if constexpr (CL == 1) {
-    // G >= 4 adjacent rows: the transposed store writes G*8-byte segments
-    x_inverse_to_global<C, NX, NY, G, NT, RS, PS, true, XG>(sm, dst, t0, p1, p12, a.v_store != 0);
-  } else {
-    // a cluster of CL CTAs holds CL*G adjacent rows: each CTA stores its share
-    // of all of them as 32-byte segments, read through distributed shared memory
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const int q = (int)cl.block_rank();
-    cl.sync();
-    if constexpr (Gm::TMA_STORE) {
-      // staging at a 128-byte aligned shared address (bulk tensor copies need it)
-      const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem_raw + Gm::STAGE_OFF);
-      C* stage = reinterpret_cast<C*>(smem_raw + Gm::STAGE_OFF + ((128u - (s0 & 127u)) & 127u));
-      x_inverse_cluster_store_tma<C, NX, NY, G, NT, RS, PS, CL>(sm, stage, &a.tmap_dst, b * N, t0 - q * G, q, p1,
-                                                                p12, a.v_store != 0);
-    } else {
-      x_inverse_cluster_store<C, NX, NY, G, NT, RS, PS, CL>(sm, dst, t0 - q * G, q, p1, p12, a.v_store != 0);
+  // Without a cluster the pass is persistent, like the in-place pass: CTA c
+  // takes tiles c, c + gridDim.x, ... (the host launches the resident count
+  // and prefetches that many tiles ahead, this CTA's next one).  A clustered
+  // launch takes one tile per CTA.
+  const int ntiles = (CL == 1) ? a.ntiles : (int)gridDim.x;
+  __syncthreads();                               // twiddles in shared memory
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int b = tile / Gm::TILES_PER_SIM;
+    const int t0 = (tile % Gm::TILES_PER_SIM) * G;
+    const C* src = a.src + (size_t)b * N * N;
+    C* dst = a.dst + (size_t)b * N * N;
+    const C* p1 = a.p1 + (size_t)b * N;
+    const C* p12 = a.p12 + (size_t)b * (2 * NX - 1) * (2 * NY - 1);
+
+    const int nt = tile + a.pref_ahead;
+    if (tid == 0 && a.pref_ahead > 0 && nt < ntiles) {
+      const C* p = a.src + (size_t)(nt / Gm::TILES_PER_SIM) * N * N + (size_t)(nt % Gm::TILES_PER_SIM) * G * N;
+      prefetch_l2(p, (unsigned)(G * N * sizeof(C)));
     }
-    cl.sync();                                   // keep this CTA's planes alive for the readers
+    x_forward_from_global<C, NX, NY, G, NT, RS, PS, false, XG>(sm, stwx, src, t0, p1, p12, a.v_load != 0, qa);
+    if constexpr (N2X > 1) x_forward_second<C, NX, NY, G, NT, RS, PS, XG>(sm, qa);
+    y_sandwich<C, NX, NY, G, NT, RS, PS>(sm, stwy, a.gy, a.qt);
+    // the transposed stores below read every column: a CTA barrier
+    if constexpr (N2X > 1) x_inverse_first<C, NX, NY, G, NT, RS, PS, XG, false>(sm, stwx);
+    if constexpr (CL == 1) {
+      // G >= 4 adjacent rows: the transposed store writes G*8-byte segments
+      x_inverse_to_global<C, NX, NY, G, NT, RS, PS, true, XG>(sm, dst, t0, p1, p12, a.v_store != 0);
+      __syncthreads();                           // the next tile overwrites the planes just read
+    } else {
+      // a cluster of CL CTAs holds CL*G adjacent rows: each CTA stores its share
+      // of all of them as 32-byte segments, read through distributed shared memory
+      namespace cg = cooperative_groups;
+      cg::cluster_group cl = cg::this_cluster();
+      const int q = (int)cl.block_rank();
+      cl.sync();
+      if constexpr (Gm::TMA_STORE) {
+        // staging at a 128-byte aligned shared address (bulk tensor copies need it)
+        const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem_raw + Gm::STAGE_OFF);
+        C* stage = reinterpret_cast<C*>(smem_raw + Gm::STAGE_OFF + ((128u - (s0 & 127u)) & 127u));
+        x_inverse_cluster_store_tma<C, NX, NY, G, NT, RS, PS, CL>(sm, stage, &a.tmap_dst, b * N, t0 - q * G, q, p1,
+                                                                  p12, a.v_store != 0);
+      } else {
+        x_inverse_cluster_store<C, NX, NY, G, NT, RS, PS, CL>(sm, dst, t0 - q * G, q, p1, p12, a.v_store != 0);
+      }
+      cl.sync();                                 // keep this CTA's planes alive for the readers
+    }
   }
 }
 
